@@ -1,0 +1,168 @@
+/*
+ * gbresample -- multinomial particle-filter resampling on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of libgbresample.so.  It computes the multinomial resampling map of
+ * arXiv 2604.01356 ("A divide and conquer strategy for multinomial particle
+ * filter resampling"):
+ *
+ *   Eq. 3   cumulative weights  W_j = sum_{k<=j} w_k / sum_k w_k,  j = 1..M
+ *   Alg. 1  N sorted uniforms    U_i = Z_i / Z_{N+1},  Z_i = sum_{k<=i} -log(v_k)
+ *           (the printed normaliser Z_{i+1} is read as Z_{N+1})
+ *   Eq. 2   r_i = P^{-1}(U_i) = the smallest j with W_j >= U_i (ties go to j,
+ *           a U above W_M is clamped to M), i = 1..N
+ *
+ * and the three maps the paper compares: divide and conquer (Alg. 5), binary
+ * search (Alg. 3 with Alg. 2) and the Carpenter-Clifford-Fearnhead linear walk
+ * (Alg. 4).  The draws v_k in (0,1) come from Philox-4x64-10 (Salmon et al.,
+ * SC'11): key = (seed, instance), counter = (k/4, 0, 0, 0), 64-bit word k mod 4;
+ * binary64 draws are (2*(x>>12)+1)*2^-53, binary32 draws (2*(x>>41)+1)*2^-24.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named w, W, U, out_* and the batched offset arrays are DEVICE
+ *    pointers owned by the caller.  The library never frees them and never
+ *    keeps them after the call returns.  Weight and output arrays must be
+ *    8-byte aligned; 16-byte alignment enables vectorised loads.
+ *  - Indices are 0-based int32: paper index j is returned as j-1.
+ *  - Sizes: M >= 1, M < 2^31; N >= 0 (N = 0 is a no-op); N > M is allowed.
+ *  - stream is a cudaStream_t (NULL = the legacy default stream).  Every call
+ *    only enqueues work on that stream and returns; it does not synchronise.
+ *  - Errors found on the host (bad sizes, NULL pointers, bad options, CUDA
+ *    launch failures, workspace allocation failure) are returned at once and
+ *    enqueue nothing.  Errors found on the device (a negative, NaN or infinite
+ *    weight; a zero total; a bounded wait that ran out) are latched in the
+ *    handle's device status word and reported by the next rs_get_status();
+ *    the outputs of that call are then unspecified but every write stays in
+ *    bounds and every kernel terminates.
+ *  - A handle owns a grow-only device workspace; calls on one handle must not
+ *    overlap (use one handle per concurrent stream).  Handles are not
+ *    thread-safe; distinct handles may be used from distinct threads.
+ */
+#ifndef GBRESAMPLE_H
+#define GBRESAMPLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rs_handle rs_handle;
+
+typedef enum {
+  RS_OK = 0,
+  RS_EINVAL = 1,      /* bad argument (size, pointer, option) */
+  RS_ENOMEM = 2,      /* workspace allocation failed */
+  RS_ECUDA = 3,       /* a CUDA runtime call failed */
+  RS_ENONFINITE = 4,  /* a weight is negative, NaN or infinite (device-detected) */
+  RS_EZEROSUM = 5,    /* the weights sum to zero (device-detected) */
+  RS_ETIMEOUT = 6     /* a bounded inter-block wait gave up (device-detected) */
+} rs_status;
+
+/* Inverse-CDF map used after the cumulative weights and uniforms exist. */
+typedef enum {
+  RS_MAP_DAC = 0,     /* Alg. 5: split U, search the split points, walk the leaves */
+  RS_MAP_BINARY = 1,  /* Alg. 3: one full-range binary search per sample */
+  RS_MAP_LINEAR = 2   /* Alg. 4: every W element visited once (merge walk) */
+} rs_map_algo;
+
+/* Arithmetic of the path.
+ *  RS_F64      binary64 weights and binary64 draws; results carry binary64
+ *              accuracy (cumulative weights within 1e-12 relative of exact).
+ *  RS_F32_COMP binary32 weights and binary32 draws; spacings and scans run in
+ *              binary32 with compensation (error-free transforms / exact
+ *              integer segment sums), binary64 only at segment boundaries and
+ *              for the final normalisation; W within 4*2^-23 of exact. */
+typedef enum { RS_F64 = 0, RS_F32_COMP = 1 } rs_precision;
+
+/* Options.  A NULL rs_opts pointer, or a zeroed struct, selects defaults. */
+typedef struct {
+  int32_t algo;        /* rs_map_algo (default RS_MAP_DAC) */
+  int32_t prec;        /* rs_precision (default RS_F64) */
+  int32_t leaf_L;      /* DaC: samples per leaf (power of two 1..1024; 0 = choose from M/N) */
+  int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 4096) */
+  int32_t spin_limit;  /* bounded-wait iterations before RS_ETIMEOUT (0 = default) */
+  int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of the
+                          weights pass withholds its look-back publication, so every
+                          later tile's bounded wait runs out and RS_ETIMEOUT is
+                          latched (results are then unspecified).  Nothing faults. */
+  int32_t reserved[2]; /* must be zero */
+} rs_opts;
+
+/* Create a handle bound to the CUDA device current on the calling thread.
+ * Allocates the device status word and an initial workspace. */
+rs_status rs_create(rs_handle** out);
+
+/* Destroy a handle and free its workspace.  Synchronises the device. */
+rs_status rs_destroy(rs_handle* h);
+
+/* Whole path from weights (Eq. 3 + Alg. 1 + Eq. 2).
+ *  w       [M] binary64 weights (opts->prec == RS_F64) or binary32 weights
+ *          (RS_F32_COMP); non-negative, finite, not all zero; unnormalised.
+ *  out_idx [N] int32 sample indices, written.
+ *  W_out   [M] binary64 cumulative weights W (Eq. 3), written if not NULL.
+ *  seed, instance select the Philox stream of the N+1 draws.
+ * The map is always the segmented divide and conquer described in the
+ * library's design notes; opts->algo is ignored here. */
+rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                        int32_t* out_idx, double* W_out, const rs_opts* opts, void* stream);
+
+/* Sampling from given cumulative weights (Alg. 1 + Eq. 2; the paper's timed
+ * "sampling steps", W excluded).
+ *  W       [M] binary64 cumulative weights, non-decreasing, W_M = 1 expected
+ *          (not checked: a U above W_M is clamped to M-1).
+ *  out_idx [N] int32, written.  opts->algo selects the map. */
+rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                        int32_t* out_idx, const rs_opts* opts, void* stream);
+
+/* Alg. 1: N sorted uniforms.  U_out [N] binary64, written.  With
+ * opts->prec == RS_F32_COMP the binary32 draws and compensated binary32
+ * arithmetic are used and the (hi+lo) result is returned widened. */
+rs_status rs_sorted_uniform(rs_handle* h, int64_t N, uint64_t seed, uint64_t instance, double* U_out,
+                            const rs_opts* opts, void* stream);
+
+/* Eq. 3: cumulative weights.  w as in rs_resample_w; W_out [M] binary64,
+ * written, non-decreasing, W_out[M-1] == 1 exactly. */
+rs_status rs_cumulative(rs_handle* h, const void* w, int64_t M, double* W_out, const rs_opts* opts, void* stream);
+
+/* Eq. 2 only: r_i = smallest j with W_j >= U_i, clamped to M-1.
+ *  W [M], U [N] binary64 (U non-decreasing for RS_MAP_DAC and RS_MAP_LINEAR);
+ *  out_idx [N] int32, written.  Bit-exact: every comparison is an exact
+ *  binary64 comparison, so all three maps return identical indices. */
+rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int64_t N, int32_t* out_idx,
+                 const rs_opts* opts, void* stream);
+
+/* Raw Philox-4x64-10 stream words first .. first+n-1 of (seed, instance).
+ * out [n] uint64, written.  Exposed so the generator can be checked bit for bit. */
+rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t first, int64_t n, uint64_t* out,
+                    void* stream);
+
+/* K independent instances in one launch sequence (the many-filter setting of
+ * Sec. I: M_k = N_k * P_k weights per filter).  Instance k owns
+ * w[w_off[k] .. w_off[k+1]) and out_idx[r_off[k] .. r_off[k+1]) and draws from
+ * the Philox stream (seed, instance = k).
+ *  w      [w_off[K]] binary32 (RS_F32_COMP, the default for this call when
+ *         opts is NULL) or binary64 (RS_F64) weights.
+ *  w_off, r_off  [K+1] int64 DEVICE arrays, non-decreasing, starting at 0;
+ *         every instance needs M_k >= 1 unless N_k = 0.
+ *  h_w_off, h_r_off  optional HOST copies of the same offsets (may be NULL);
+ *         when given, the host orders instances by size without a device read.
+ *  out_idx [r_off[K]] int32 indices, local to each instance, written. */
+rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
+                              const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
+                              const rs_opts* opts, void* stream);
+
+/* Synchronise `stream`, return the device status latched since the previous
+ * call (RS_OK if none) and clear it. */
+rs_status rs_get_status(rs_handle* h, void* stream);
+
+/* Text of the last host-side error on this handle ("" if none). */
+const char* rs_last_error(rs_handle* h);
+
+/* Library version string. */
+const char* rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBRESAMPLE_H */

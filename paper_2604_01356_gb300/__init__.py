@@ -1,0 +1,16 @@
+"""GB300-native multinomial resampling (arXiv 2604.01356).
+
+Thin Python binding over the C ABI of ``libgbresample.so`` (declared in
+``include/gbresample.h``).  Functions keep the C names; tensors are passed as
+device pointers and the current torch CUDA stream is used unless one is
+given.  Every computation runs in the library's CUDA kernels: there is no
+CPU path, and importing fails loudly when the library is missing.
+"""
+from ._binding import (  # noqa: F401
+    RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_EZEROSUM, RS_ETIMEOUT, RS_OK,
+    RS_F32_COMP, RS_F64, RS_MAP_BINARY, RS_MAP_DAC, RS_MAP_LINEAR,
+    ResampleError, Handle, lib, library_path, opts,
+    rs_create, rs_destroy, rs_get_status, rs_last_error, rs_version,
+    rs_resample_w, rs_resample_W, rs_sorted_uniform, rs_cumulative, rs_map, rs_philox,
+    rs_resample_batched,
+)

@@ -1,0 +1,452 @@
+// Host side of the C ABI declared in include/gbresample.h: argument checks,
+// the grow-only device workspace, launch sequencing and the device status
+// word.  Every entry point enqueues on the caller's stream and returns.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gbresample.h"
+#include "internal.h"
+
+struct rs_handle {
+  int device = 0;
+  int* status = nullptr;  // device status word (first device error wins)
+  void* ws = nullptr;     // grow-only workspace
+  size_t ws_bytes = 0;
+  std::string err;
+};
+
+namespace gbr {
+
+int num_sms() {
+  static int cached[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+  }
+  return cached[dev];
+}
+
+}  // namespace gbr
+
+namespace {
+
+using namespace gbr;
+
+constexpr long long kMaxLen = (1LL << 31) - 1;
+constexpr int kDefaultSpin = 1 << 22;
+constexpr int kStageCap = 512;  // shared-memory staging capacity of the DaC leaf (per warp)
+
+rs_status fail(rs_handle* h, rs_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+rs_status cuda_fail(rs_handle* h, cudaError_t e, const char* where) {
+  if (h) h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return RS_ECUDA;
+}
+#define RS_CK(h, call)                                        \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
+  } while (0)
+
+struct Opts {
+  int algo = RS_MAP_DAC;
+  int prec = RS_F64;
+  int leaf_L = 0;
+  int stage_max = kStageCap;
+  int spin = kDefaultSpin;
+  int debug = 0;
+};
+
+rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec) {
+  Opts r;
+  r.prec = default_prec;
+  if (o) {
+    if (o->algo < 0 || o->algo > 2) return fail(h, RS_EINVAL, "opts.algo out of range");
+    if (o->prec < 0 || o->prec > 1) return fail(h, RS_EINVAL, "opts.prec out of range");
+    if (o->leaf_L < 0 || o->leaf_L > 1024 || (o->leaf_L & (o->leaf_L - 1)))
+      return fail(h, RS_EINVAL, "opts.leaf_L must be 0 or a power of two <= 1024");
+    if (o->stage_max < 0) return fail(h, RS_EINVAL, "opts.stage_max negative");
+    if (o->spin_limit < 0) return fail(h, RS_EINVAL, "opts.spin_limit negative");
+    for (int i = 0; i < 2; ++i)
+      if (o->reserved[i]) return fail(h, RS_EINVAL, "opts.reserved must be zero");
+    if (o->debug_flags & ~1) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
+    r.debug = o->debug_flags;
+    r.algo = o->algo;
+    r.prec = o->prec;
+    r.leaf_L = o->leaf_L;
+    if (o->stage_max) r.stage_max = o->stage_max < kStageCap ? o->stage_max : kStageCap;
+    if (o->spin_limit) r.spin = o->spin_limit;
+  }
+  *out = r;
+  return RS_OK;
+}
+
+// Carves the single workspace allocation into 256-byte aligned regions.
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+rs_status ensure_ws(rs_handle* h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return RS_OK;
+  size_t want = h->ws_bytes ? h->ws_bytes : (size_t)1 << 20;
+  while (want < bytes) want *= 2;
+  if (h->ws) {
+    cudaError_t e = cudaFree(h->ws);  // implicitly waits for work using it
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaFree(workspace)");
+  }
+  cudaError_t e = cudaMalloc(&h->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return fail(h, RS_ENOMEM, "workspace allocation of " + std::to_string(want) + " bytes failed");
+  }
+  h->ws_bytes = want;
+  return RS_OK;
+}
+
+// Regions of one call.  The counters and look-back descriptors sit first so
+// that a single memset clears them.
+struct Plan {
+  // weights side
+  long long M = 0, nseg = 0, wtiles = 0;
+  int nlev = 0;
+  long long lvl_n[kMaxLevels] = {0};
+  size_t o_wdesc = 0, o_seg = 0, o_lvl[kMaxLevels] = {0}, o_total = 0;
+  // uniforms side
+  long long N = 0, ndraw = 0, utiles = 0;
+  size_t o_udesc = 0, o_Z = 0, o_Ztot = 0, o_U = 0;
+  size_t o_ctr = 0, clear_bytes = 0, bytes = 0;
+};
+
+Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) {
+  Plan p;
+  Layout L;
+  p.o_ctr = L.take(256);  // [0]: uniform tile counter, [1]: weight tile counter
+  if (need_u) {
+    p.N = N;
+    p.ndraw = N + 1;
+    p.utiles = (p.ndraw + kUTile - 1) / kUTile;
+    p.o_udesc = L.take((size_t)p.utiles * kTileDescBytes);
+  }
+  if (need_w) {
+    p.M = M;
+    p.nseg = (M + kSegLen - 1) / kSegLen;
+    p.wtiles = (M + kWTile - 1) / kWTile;
+    p.o_wdesc = L.take((size_t)p.wtiles * kTileDescBytes);
+  }
+  p.clear_bytes = L.off;
+  if (need_w) {
+    p.o_seg = L.take((size_t)p.nseg * sizeof(SegRec));
+    long long n = p.nseg;
+    p.nlev = 0;
+    while (true) {
+      p.lvl_n[p.nlev] = n;
+      p.o_lvl[p.nlev] = L.take((size_t)n * 8);
+      ++p.nlev;
+      if (n <= 32 || p.nlev == kMaxLevels) break;
+      n = (n + 31) / 32;
+    }
+    p.o_total = L.take(16);
+  }
+  if (need_u) {
+    p.o_Z = L.take((size_t)(N > 0 ? N : 1) * 16);
+    p.o_Ztot = L.take(16);
+    if (need_U) p.o_U = L.take((size_t)(N > 0 ? N : 1) * 8);
+  }
+  p.bytes = L.off;
+  return p;
+}
+
+SegIndex index_of(rs_handle* h, const Plan& p) {
+  SegIndex idx;
+  memset(&idx, 0, sizeof(idx));
+  idx.nseg = p.nseg;
+  idx.nlev = p.nlev;
+  for (int l = 0; l < p.nlev; ++l) {
+    idx.lvl_n[l] = p.lvl_n[l];
+    idx.lvl[l] = reinterpret_cast<unsigned long long*>(static_cast<char*>(h->ws) + p.o_lvl[l]);
+  }
+  return idx;
+}
+
+template <typename P>
+P* at(rs_handle* h, size_t off) {
+  return reinterpret_cast<P*>(static_cast<char*>(h->ws) + off);
+}
+unsigned* ctr_u(rs_handle* h, const Plan& p) { return at<unsigned>(h, p.o_ctr); }
+unsigned* ctr_w(rs_handle* h, const Plan& p) { return at<unsigned>(h, p.o_ctr) + 1; }
+
+rs_status check_handle(rs_handle* h) {
+  if (!h) return RS_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "cudaGetDevice");
+  if (dev != h->device) return fail(h, RS_EINVAL, "handle belongs to another CUDA device than the current one");
+  h->err.clear();
+  return RS_OK;
+}
+
+rs_status check_sizes(rs_handle* h, long long M, long long N) {
+  if (M < 1 || M > kMaxLen) return fail(h, RS_EINVAL, "M must satisfy 1 <= M < 2^31");
+  if (N < 0 || N > kMaxLen) return fail(h, RS_EINVAL, "N must satisfy 0 <= N < 2^31");
+  return RS_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Samples per warp group of the segmented map: about two warps' worth of
+// groups per SM slot, at least one sample each.
+int group_size(long long N) {
+  const long long target = (long long)num_sms() * 64;
+  long long G = (N + target - 1) / target;
+  if (G < 1) G = 1;
+  if (G > (1 << 20)) G = 1 << 20;
+  return (int)G;
+}
+
+// DaC leaf size: the largest power of two L <= 256 whose expected W range
+// (L*M/N elements) fits the staging capacity; 1 when samples are sparse.
+int leaf_size(const Opts& o, long long M, long long N) {
+  if (o.leaf_L > 0) return o.leaf_L;
+  double cap = (double)o.stage_max * (double)N / (double)M;
+  int L = 1;
+  while (L * 2 <= 256 && L * 2 <= cap) L *= 2;
+  return L;
+}
+
+rs_status enqueue_uniforms(rs_handle* h, const Plan& p, bool f32, uint64_t seed, uint64_t inst, double* U_out,
+                           const Opts& o, cudaStream_t st) {
+  RS_CK(h, launch_uniform_scan(f32, p.ndraw, seed, inst, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot),
+                               at<void>(h, p.o_udesc), ctr_u(h, p), h->status, o.spin, st));
+  RS_CK(h, launch_uniform_norm(f32, p.N, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot), U_out, st));
+  return RS_OK;
+}
+
+rs_status enqueue_map(rs_handle* h, const Opts& o, const double* W, long long M, const double* U, long long N,
+                      int32_t* out, cudaStream_t st) {
+  switch (o.algo) {
+    case RS_MAP_BINARY: RS_CK(h, launch_map_binary(W, M, U, N, out, st)); break;
+    case RS_MAP_LINEAR: RS_CK(h, launch_map_linear(W, M, U, N, out, st)); break;
+    default: RS_CK(h, launch_map_dac(W, M, U, N, leaf_size(o, M, N), o.stage_max, out, st)); break;
+  }
+  return RS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rs_version(void) { return "gbresample 0.1 (sm_103a)"; }
+
+rs_status rs_create(rs_handle** out) {
+  if (!out) return RS_EINVAL;
+  *out = nullptr;
+  rs_handle* h = new (std::nothrow) rs_handle();
+  if (!h) return RS_ENOMEM;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = init_log_table();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (h->status) cudaFree(h->status);
+    delete h;
+    return RS_ECUDA;
+  }
+  *out = h;
+  return RS_OK;
+}
+
+rs_status rs_destroy(rs_handle* h) {
+  if (!h) return RS_EINVAL;
+  cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
+  if (h->ws) e1 = cudaFree(h->ws);
+  if (h->status) e2 = cudaFree(h->status);
+  delete h;
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? RS_OK : RS_ECUDA;
+}
+
+const char* rs_last_error(rs_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+rs_status rs_get_status(rs_handle* h, void* stream) {
+  if (!h) return RS_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_CK(h, cudaStreamSynchronize(st));
+  int v = 0;
+  RS_CK(h, cudaMemcpy(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  RS_CK(h, cudaMemset(h->status, 0, sizeof(int)));
+  if (v < 0 || v > RS_ETIMEOUT) v = RS_ECUDA;
+  return (rs_status)v;
+}
+
+rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t first, int64_t n, uint64_t* out,
+                    void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  if (n < 0) return fail(h, RS_EINVAL, "n must be >= 0");
+  if (n == 0) return RS_OK;
+  if (!out || !aligned(out, 8)) return fail(h, RS_EINVAL, "out must be a non-NULL 8-byte aligned device pointer");
+  RS_CK(h, launch_philox(seed, instance, first, n, reinterpret_cast<unsigned long long*>(out),
+                         static_cast<cudaStream_t>(stream)));
+  return RS_OK;
+}
+
+rs_status rs_sorted_uniform(rs_handle* h, int64_t N, uint64_t seed, uint64_t instance, double* U_out,
+                            const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if (N < 0 || N > kMaxLen) return fail(h, RS_EINVAL, "N must satisfy 0 <= N < 2^31");
+  if (N == 0) return RS_OK;
+  if (!U_out || !aligned(U_out, 8)) return fail(h, RS_EINVAL, "U_out must be a non-NULL 8-byte aligned pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(0, N, false, true, false);
+  if ((s = ensure_ws(h, p.bytes))) return s;
+  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  return enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, U_out, o, st);
+}
+
+rs_status rs_cumulative(rs_handle* h, const void* w, int64_t M, double* W_out, const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if ((s = check_sizes(h, M, 0))) return s;
+  const bool f32 = o.prec == RS_F32_COMP;
+  if (!w || !aligned(w, f32 ? 4 : 8)) return fail(h, RS_EINVAL, "w must be a non-NULL aligned device pointer");
+  if (!W_out || !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be a non-NULL 8-byte aligned pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(M, 0, true, false, false);
+  if ((s = ensure_ws(h, p.bytes))) return s;
+  const bool vec = aligned(w, 16);
+  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  const SegIndex idx = index_of(h, p);
+  RS_CK(h, launch_w_pass1(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_wdesc), ctr_w(h, p),
+                          at<void>(h, p.o_total), h->status, o.spin, o.debug & 1, st));
+  RS_CK(h, launch_w_write(f32, vec, w, M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_total), W_out, h->status, st));
+  return RS_OK;
+}
+
+rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                        int32_t* out_idx, double* W_out, const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if ((s = check_sizes(h, M, N))) return s;
+  const bool f32 = o.prec == RS_F32_COMP;
+  if (!w || !aligned(w, f32 ? 4 : 8)) return fail(h, RS_EINVAL, "w must be a non-NULL aligned device pointer");
+  if (N > 0 && (!out_idx || !aligned(out_idx, 4))) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  if (W_out && !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be 8-byte aligned");
+  if (N == 0 && !W_out) return RS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(M, N, true, N > 0, N > 0);
+  if ((s = ensure_ws(h, p.bytes))) return s;
+  const bool vec = aligned(w, 16);
+  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  if (N > 0) {
+    if ((s = enqueue_uniforms(h, p, f32, seed, instance, at<double>(h, p.o_U), o, st))) return s;
+  }
+  const SegIndex idx = index_of(h, p);
+  RS_CK(h, launch_w_pass1(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_wdesc), ctr_w(h, p),
+                          at<void>(h, p.o_total), h->status, o.spin, o.debug & 1, st));
+  if (N > 0)
+    RS_CK(h, launch_map_seg(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_total), at<double>(h, p.o_U),
+                            N, group_size(N), out_idx, st));
+  if (W_out)
+    RS_CK(h, launch_w_write(f32, vec, w, M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_total), W_out, h->status, st));
+  return RS_OK;
+}
+
+rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                        int32_t* out_idx, const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if ((s = check_sizes(h, M, N))) return s;
+  if (N == 0) return RS_OK;
+  if (!W || !aligned(W, 8)) return fail(h, RS_EINVAL, "W must be a non-NULL 8-byte aligned pointer");
+  if (!out_idx || !aligned(out_idx, 4)) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Plan p = make_plan(0, N, false, true, true);
+  if ((s = ensure_ws(h, p.bytes))) return s;
+  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  if ((s = enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, at<double>(h, p.o_U), o, st))) return s;
+  return enqueue_map(h, o, W, M, at<double>(h, p.o_U), N, out_idx, st);
+}
+
+rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int64_t N, int32_t* out_idx,
+                 const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if ((s = check_sizes(h, M, N))) return s;
+  if (N == 0) return RS_OK;
+  if (!W || !aligned(W, 8) || !U || !aligned(U, 8)) return fail(h, RS_EINVAL, "W and U must be 8-byte aligned");
+  if (!out_idx || !aligned(out_idx, 4)) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  return enqueue_map(h, o, W, M, U, N, out_idx, static_cast<cudaStream_t>(stream));
+}
+
+rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
+                              const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
+                              const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F32_COMP))) return s;
+  if (K < 0) return fail(h, RS_EINVAL, "K must be >= 0");
+  if (K == 0) return RS_OK;
+  if (!w || !w_off || !r_off) return fail(h, RS_EINVAL, "w, w_off and r_off must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<int64_t> wo, ro;
+  if (h_w_off && h_r_off) {
+    wo.assign(h_w_off, h_w_off + K + 1);
+    ro.assign(h_r_off, h_r_off + K + 1);
+  } else {
+    wo.resize(K + 1);
+    ro.resize(K + 1);
+    RS_CK(h, cudaMemcpyAsync(wo.data(), w_off, (K + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RS_CK(h, cudaMemcpyAsync(ro.data(), r_off, (K + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RS_CK(h, cudaStreamSynchronize(st));
+  }
+  if (wo[0] != 0 || ro[0] != 0) return fail(h, RS_EINVAL, "offsets must start at 0");
+  for (int32_t k = 0; k < K; ++k) {
+    const long long Mk = wo[k + 1] - wo[k], Nk = ro[k + 1] - ro[k];
+    if (Mk < 0 || Nk < 0) return fail(h, RS_EINVAL, "offsets must be non-decreasing");
+    if (Nk > 0 && Mk < 1) return fail(h, RS_EINVAL, "an instance with samples needs at least one weight");
+    if (Mk > kMaxLen || Nk > kMaxLen) return fail(h, RS_EINVAL, "instance too large");
+  }
+  const size_t esz = o.prec == RS_F32_COMP ? 4 : 8;
+  rs_opts one;
+  memset(&one, 0, sizeof(one));
+  one.prec = o.prec;
+  one.spin_limit = o.spin;
+  for (int32_t k = 0; k < K; ++k) {
+    const long long Mk = wo[k + 1] - wo[k], Nk = ro[k + 1] - ro[k];
+    if (Nk == 0) continue;
+    const void* wk = static_cast<const char*>(w) + (size_t)wo[k] * esz;
+    if ((s = rs_resample_w(h, wk, Mk, Nk, seed, (uint64_t)k, out_idx + ro[k], nullptr, &one, stream))) return s;
+  }
+  return RS_OK;
+}
+
+}  // extern "C"

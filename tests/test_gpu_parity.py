@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA path through the C ABI against the oracle.
+
+Bit-exact where the work is integer or exact comparison (Philox words, the
+three maps on given W and U); within the derived tolerance where floating
+point is involved (cumulative weights, uniforms); boundary-only index
+differences end to end.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity_util import ABS_F32, REL_F64, assert_boundary_only
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2604_01356_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def h(g):
+    hd = g.Handle()
+    yield hd
+    hd.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------- Philox ----
+@pytest.mark.parametrize("seed,inst,first,n", [(0, 0, 0, 4096), (12, 3, 1, 1001), (2**64 - 1, 2**63, 2**40 - 3, 777),
+                                               (99, 0, 5, 100_003)])
+def test_philox_words_bit_exact(g, h, seed, inst, first, n):
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    g.rs_philox(h.h, seed, inst, first, n, out)
+    got = host(out).view(np.uint64)
+    if first == 0 and n <= 4096:
+        ref = oracle.stream_words(seed, inst, n)
+    else:
+        ks = np.unique(np.concatenate([np.arange(min(n, 64)), np.linspace(0, n - 1, 200).astype(np.int64)]))
+        L = oracle.lib()
+        ref_s = np.array([L.orc_stream_word(seed, inst, first + int(k)) for k in ks], dtype=np.uint64)
+        assert np.array_equal(got[ks], ref_s)
+        return
+    assert np.array_equal(got, ref)
+
+
+# ----------------------------------------------------------- uniforms ----
+@pytest.mark.parametrize("N", [1, 2, 31, 4095, 4096, 4097, 3 * 4096 + 77, 100_000])
+def test_sorted_uniform_f64(g, h, N):
+    U = torch.empty(N, dtype=torch.float64, device="cuda")
+    g.rs_sorted_uniform(h.h, N, 5, 7, U)
+    assert h.status() == g.RS_OK
+    got = host(U)
+    ref = oracle.sorted_uniform(N, 5, 7)
+    assert np.all(np.diff(got) >= 0)
+    assert got[0] > 0 and got[-1] <= 1.0
+    rel = np.max(np.abs(got - ref) / ref)
+    assert rel <= 1e-13, rel
+
+
+@pytest.mark.parametrize("N", [1, 4097, 65_536])
+def test_sorted_uniform_f32_comp(g, h, N):
+    U = torch.empty(N, dtype=torch.float64, device="cuda")
+    g.rs_sorted_uniform(h.h, N, 9, 1, U, g.opts(prec=g.RS_F32_COMP))
+    assert h.status() == g.RS_OK
+    got = host(U)
+    ref = oracle.sorted_uniform(N, 9, 1, single=True)
+    assert np.all(np.diff(got) >= 0)
+    assert np.max(np.abs(got - ref)) <= ABS_F32
+
+
+# ----------------------------------------------------- cumulative (Eq.3) --
+SIZES = [1, 2, 511, 512, 513, 4095, 4096, 4097, 37 * 4096 + 123]
+
+
+@pytest.mark.parametrize("M", SIZES)
+def test_cumulative_f64_sizes(g, h, M):
+    w = workloads.weights_lognormal(M, 2.0, seed=M)
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, dev(w), M, W)
+    assert h.status() == g.RS_OK
+    got = host(W)
+    ref, _ = oracle.cumulative(w)
+    assert got[-1] == 1.0
+    assert np.all(np.diff(got) >= 0)
+    assert np.all(np.abs(got - ref) <= REL_F64 * ref + 1e-300)
+
+
+@pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
+def test_cumulative_f64_adversarial(g, h, kind):
+    M = 9 * 4096 + 5
+    w = workloads.adversarial_weights(kind, M, seed=2)
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, dev(w), M, W)
+    assert h.status() == g.RS_OK
+    got = host(W)
+    ref, _ = oracle.cumulative(w)
+    assert got[-1] == 1.0 and np.all(np.diff(got) >= 0)
+    assert np.all(np.abs(got - ref) <= REL_F64 * ref + 1e-300), kind
+
+
+@pytest.mark.parametrize("M", [513, 4097, 50_003])
+def test_cumulative_f32_comp(g, h, M):
+    w = workloads.weights_lognormal(M, 1.5, seed=M).astype(np.float32)
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, dev(w), M, W, g.opts(prec=g.RS_F32_COMP))
+    assert h.status() == g.RS_OK
+    got = host(W)
+    ref, _ = oracle.cumulative(w)
+    assert got[-1] == 1.0 and np.all(np.diff(got) >= 0)
+    assert np.max(np.abs(got - ref)) <= ABS_F32
+
+
+# ---------------------------------------------------- maps, bit-exact ----
+def _map_case(kind, M, N, seed):
+    rng = np.random.default_rng(seed)
+    w = workloads.adversarial_weights(kind, M, seed) if kind in workloads.ADVERSARIAL else \
+        workloads.weights_lognormal(M, 2.0, seed)
+    W, _ = oracle.cumulative(w)
+    # sorted u's including exact ties with W, values above W_M and tiny values
+    picks = W[rng.integers(0, M, size=min(N, 64))]
+    U = np.sort(np.concatenate([rng.random(max(N - picks.size - 2, 0)), picks, [1e-300, 1.0]])[:N])
+    return W, U
+
+
+MAP_CASES = [("lognormal", 4096, 1024), ("lognormal", 16 * 4096 + 7, 300), ("lognormal", 1000, 5000),
+             ("zeros_runs", 20_000, 2000), ("dyadic", 3000, 3000), ("spike", 5000, 100), ("first", 700, 64),
+             ("last", 700, 64), ("lognormal", 1, 10), ("lognormal", 2, 1), ("equal", 4096, 4096),
+             ("lognormal", 300_000, 4099)]
+
+
+@pytest.mark.parametrize("algo", ["dac", "binary", "linear"])
+@pytest.mark.parametrize("kind,M,N", MAP_CASES)
+def test_map_bit_exact(g, h, algo, kind, M, N):
+    W, U = _map_case(kind, M, N, seed=M + N)
+    ref = oracle.inverse_cdf_walk(W, U)
+    if M * N <= 5_000_000:
+        assert np.array_equal(ref, oracle.inverse_cdf(W, U))
+    a = {"dac": g.RS_MAP_DAC, "binary": g.RS_MAP_BINARY, "linear": g.RS_MAP_LINEAR}[algo]
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.rs_map(h.h, dev(W), M, dev(U), N, out, g.opts(algo=a))
+    got = host(out)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("L", [1, 2, 8, 32, 64, 256])
+def test_map_dac_leaf_sizes(g, h, L):
+    W, U = _map_case("lognormal", 50_000, 6000, seed=L)
+    ref = oracle.inverse_cdf_walk(W, U)
+    out = torch.empty(U.size, dtype=torch.int32, device="cuda")
+    g.rs_map(h.h, dev(W), W.size, dev(U), U.size, out, g.opts(algo=g.RS_MAP_DAC, leaf_L=L))
+    assert np.array_equal(host(out), ref)
+
+
+# --------------------------------------------------------- end to end ----
+E2E = [(4096, 1024), (37 * 4096 + 123, 3 * 4096 + 77), (1, 5), (513, 1), (2000, 9000), (200_000, 200_000)]
+
+
+@pytest.mark.parametrize("M,N", E2E)
+def test_resample_w_f64(g, h, M, N):
+    w = workloads.weights_lognormal(M, 2.0, seed=M + 1)
+    seed = 1234 + M
+    r_ref, W_ref, U_ref = oracle.resample(w, N, seed)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    Wd = torch.empty(M, dtype=torch.float64, device="cuda")
+    g.rs_resample_w(h.h, dev(w), M, N, seed, 0, out, Wd)
+    assert h.status() == g.RS_OK
+    r = host(out)
+    assert_boundary_only(r, r_ref, W_ref, U_ref, rel=REL_F64)
+    Wg = host(Wd)
+    assert Wg[-1] == 1.0 and np.all(np.abs(Wg - W_ref) <= REL_F64 * W_ref + 1e-300)
+
+
+@pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
+def test_resample_w_adversarial(g, h, kind):
+    M, N = 5 * 4096 + 17, 4096
+    w = workloads.adversarial_weights(kind, M, seed=3)
+    r_ref, W_ref, U_ref = oracle.resample(w, N, 77)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, dev(w), M, N, 77, 0, out)
+    assert h.status() == g.RS_OK
+    r = host(out)
+    assert_boundary_only(r, r_ref, W_ref, U_ref, rel=REL_F64)
+    # zero-weight indices are never drawn
+    assert np.all(w[r] > 0)
+
+
+@pytest.mark.parametrize("M,N", [(4096, 1024), (9 * 4096 + 3, 5000)])
+def test_resample_w_f32_comp(g, h, M, N):
+    w = workloads.weights_lognormal(M, 1.5, seed=M).astype(np.float32)
+    r_ref, W_ref, U_ref = oracle.resample(w, N, 31, single=True)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, dev(w), M, N, 31, 0, out, None, g.opts(prec=g.RS_F32_COMP))
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+
+
+@pytest.mark.parametrize("algo", ["dac", "binary", "linear"])
+def test_resample_W_map_only(g, h, algo):
+    M, N = 100_000, 3000
+    w = workloads.weights_lognormal(M, 2.0, seed=4)
+    W, _ = oracle.cumulative(w)
+    U_ref = oracle.sorted_uniform(N, 8, 0)
+    r_ref = oracle.inverse_cdf_walk(W, U_ref)
+    a = {"dac": g.RS_MAP_DAC, "binary": g.RS_MAP_BINARY, "linear": g.RS_MAP_LINEAR}[algo]
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.rs_resample_W(h.h, dev(W), M, N, 8, 0, out, g.opts(algo=a))
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W, U_ref, rel=REL_F64)
+
+
+def test_resample_batched_matches_instances(g, h):
+    w, woff, roff = workloads.weights_batched(K=24, seed=5, nmin=8, nmax=300, pmax=9)
+    K = 24
+    r_ref = oracle.resample_batched(w, woff, roff, seed=3, single=True)
+    out = torch.empty(int(roff[-1]), dtype=torch.int32, device="cuda")
+    g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), K, 3, out, woff, roff)
+    assert h.status() == g.RS_OK
+    got = host(out)
+    for k in range(K):
+        a, b = int(roff[k]), int(roff[k + 1])
+        wk = w[woff[k]:woff[k + 1]]
+        Wk, _ = oracle.cumulative(wk)
+        Uk = oracle.sorted_uniform(b - a, 3, k, single=True)
+        assert_boundary_only(got[a:b], r_ref[a:b], Wk, Uk, abs_tol=ABS_F32, max_frac=0.05)
+
+
+# ----------------------------------------------------- device errors ----
+@pytest.mark.parametrize("bad,code", [(-1.0, "RS_ENONFINITE"), (np.nan, "RS_ENONFINITE"), (np.inf, "RS_ENONFINITE")])
+def test_invalid_weight_latches_status(g, h, bad, code):
+    w = workloads.weights_small(20_000, seed=1)
+    w[12_345] = bad
+    out = torch.empty(100, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, dev(w), w.size, 100, 1, 0, out)
+    assert h.status() == getattr(g, code)
+    assert h.status() == g.RS_OK  # cleared
+    r = host(out)
+    assert r.min() >= 0 and r.max() < w.size  # outputs stay in bounds
+
+
+def test_zero_sum_latches_status(g, h):
+    w = np.zeros(5000)
+    out = torch.empty(10, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, dev(w), w.size, 10, 1, 0, out)
+    assert h.status() == g.RS_EZEROSUM
+
+
+def test_bounded_wait_times_out_and_context_survives(g, h):
+    """Fault injection on the host side: the first look-back tile withholds
+    its publication; every later tile's wait runs out after spin_limit polls."""
+    M = 64 * 4096
+    w = workloads.weights_small(M, seed=2)
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, dev(w), M, W, g.opts(spin_limit=200, debug_flags=1))
+    assert h.status() == g.RS_ETIMEOUT
+    # the context is still usable and a normal call is correct again
+    g.rs_cumulative(h.h, dev(w), M, W)
+    assert h.status() == g.RS_OK
+    ref, _ = oracle.cumulative(w)
+    assert np.all(np.abs(host(W) - ref) <= REL_F64 * ref)
+
+
+def test_host_argument_errors(g, h):
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    w = torch.ones(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(g.ResampleError) as e:
+        g.rs_resample_w(h.h, w, 0, 4, 1, 0, out)
+    assert e.value.code == g.RS_EINVAL
+    with pytest.raises(g.ResampleError):
+        g.rs_resample_w(h.h, w, 8, -1, 1, 0, out)
+    with pytest.raises(g.ResampleError):
+        g.rs_map(h.h, w, 8, w, 4, out, g.opts(algo=7))
+    with pytest.raises(g.ResampleError):
+        g.rs_resample_w(h.h, None, 8, 4, 1, 0, out)
+    g.rs_resample_w(h.h, w, 8, 0, 1, 0, None)  # N = 0 is a no-op
+    assert h.status() == g.RS_OK
