@@ -161,6 +161,21 @@ const char* rs_last_error(rs_handle* h);
 /* Library version string. */
 const char* rs_version(void);
 
+/* Tracing (profiling aid).  While enabled, every kernel the handle launches
+ * is bracketed by a pair of CUDA events recorded on the launch stream (also
+ * inside CUDA-graph capture, where they become event nodes).
+ *  rs_trace_enable  on != 0 starts recording; 0 stops and drops pending pairs.
+ *  rs_trace_collect synchronises the device, adds the elapsed time of every
+ *                   pending pair to per-kernel totals; keep != 0 keeps the
+ *                   pairs (a captured graph re-records them on each replay).
+ *  rs_trace_report  writes "name launches total_ms" lines into buf (NUL
+ *                   terminated, truncated to cap bytes) and returns RS_OK.
+ *  rs_trace_reset   clears the totals. */
+rs_status rs_trace_enable(rs_handle* h, int on);
+rs_status rs_trace_collect(rs_handle* h, int keep);
+rs_status rs_trace_report(rs_handle* h, char* buf, int64_t cap);
+rs_status rs_trace_reset(rs_handle* h);
+
 #ifdef __cplusplus
 }
 #endif

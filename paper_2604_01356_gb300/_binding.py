@@ -58,6 +58,10 @@ def lib():
             "rs_map": (_ST, [_P, _P, _I64, _P, _I64, _P, _OPTS, _P]),
             "rs_philox": (_ST, [_P, _U64, _U64, _U64, _I64, _P, _P]),
             "rs_resample_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _P]),
+            "rs_trace_enable": (_ST, [_P, ctypes.c_int]),
+            "rs_trace_collect": (_ST, [_P, ctypes.c_int]),
+            "rs_trace_report": (_ST, [_P, ctypes.c_char_p, _I64]),
+            "rs_trace_reset": (_ST, [_P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -150,6 +154,29 @@ def rs_resample_batched(h, w, w_off, r_off, K, seed, out_idx, h_w_off=None, h_r_
     hr = h_r_off.ctypes.data if h_r_off is not None else None
     _check(h, lib().rs_resample_batched(h, _ptr(w), _ptr(w_off), _ptr(r_off), K, hw, hr, seed, _ptr(out_idx), _opt(o),
                                         _stream(stream)))
+
+
+def rs_trace_enable(h, on=True):
+    _check(h, lib().rs_trace_enable(h, int(bool(on))))
+
+
+def rs_trace_collect(h, keep=False):
+    _check(h, lib().rs_trace_collect(h, int(bool(keep))))
+
+
+def rs_trace_report(h):
+    """{kernel name: (launches, total_ms)} accumulated by rs_trace_collect."""
+    buf = ctypes.create_string_buffer(8192)
+    _check(h, lib().rs_trace_report(h, buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, n, ms = line.split()
+        out[name] = (int(n), float(ms))
+    return out
+
+
+def rs_trace_reset(h):
+    _check(h, lib().rs_trace_reset(h))
 
 
 class Handle:

@@ -10,12 +10,27 @@
 #include "../../include/gbresample.h"
 #include "internal.h"
 
+struct rs_trace_pair {
+  const char* name;
+  cudaEvent_t start, stop;
+};
+struct rs_trace_total {
+  const char* name;
+  long long launches;
+  double ms;
+};
+
 struct rs_handle {
   int device = 0;
   int* status = nullptr;  // device status word (first device error wins)
   void* ws = nullptr;     // grow-only workspace
   size_t ws_bytes = 0;
   std::string err;
+  cudaStream_t side = nullptr;    // second stream for work independent of the weights pass
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool tracing = false;
+  std::vector<rs_trace_pair> pending;
+  std::vector<rs_trace_total> totals;
 };
 
 namespace gbr {
@@ -56,6 +71,31 @@ rs_status cuda_fail(rs_handle* h, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
   } while (0)
+
+// Event pair around one launch when the handle is tracing.
+struct TraceScope {
+  rs_handle* h;
+  cudaStream_t st;
+  rs_trace_pair p{nullptr, nullptr, nullptr};
+  TraceScope(rs_handle* h_, const char* name, cudaStream_t st_) : h(h_), st(st_) {
+    if (!h->tracing) return;
+    p.name = name;
+    if (cudaEventCreate(&p.start) != cudaSuccess || cudaEventCreate(&p.stop) != cudaSuccess) {
+      cudaGetLastError();
+      p.name = nullptr;
+      return;
+    }
+    // External records become event nodes when the stream is being captured
+    // into a CUDA graph, and behave as plain records otherwise.
+    cudaEventRecordWithFlags(p.start, st, cudaEventRecordExternal);
+  }
+  ~TraceScope() {
+    if (!p.name) return;
+    cudaEventRecordWithFlags(p.stop, st, cudaEventRecordExternal);
+    h->pending.push_back(p);
+  }
+};
+#define RS_TRACE(h, name, st) TraceScope trace_scope_(h, name, st)
 
 struct Opts {
   int algo = RS_MAP_DAC;
@@ -127,7 +167,7 @@ struct Plan {
   long long M = 0, nseg = 0, wtiles = 0;
   int nlev = 0;
   long long lvl_n[kMaxLevels] = {0};
-  size_t o_wdesc = 0, o_seg = 0, o_lvl[kMaxLevels] = {0}, o_total = 0;
+  size_t o_wdesc = 0, o_seg = 0, o_tagg = 0, o_lvl[kMaxLevels] = {0}, o_consts = 0;
   // uniforms side
   long long N = 0, ndraw = 0, utiles = 0;
   size_t o_udesc = 0, o_Z = 0, o_Ztot = 0, o_U = 0;
@@ -147,12 +187,13 @@ Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) 
   if (need_w) {
     p.M = M;
     p.nseg = (M + kSegLen - 1) / kSegLen;
-    p.wtiles = (M + kWTile - 1) / kWTile;
+    p.wtiles = (p.nseg + kSegPrefixTile - 1) / kSegPrefixTile;
     p.o_wdesc = L.take((size_t)p.wtiles * kTileDescBytes);
   }
   p.clear_bytes = L.off;
   if (need_w) {
     p.o_seg = L.take((size_t)p.nseg * sizeof(SegRec));
+    p.o_tagg = L.take((size_t)((p.nseg + 7) / 8) * kTileAggBytes);
     long long n = p.nseg;
     p.nlev = 0;
     while (true) {
@@ -162,7 +203,7 @@ Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) 
       if (n <= 32 || p.nlev == kMaxLevels) break;
       n = (n + 31) / 32;
     }
-    p.o_total = L.take(16);
+    p.o_consts = L.take(sizeof(PathConsts));
   }
   if (need_u) {
     p.o_Z = L.take((size_t)(N > 0 ? N : 1) * 16);
@@ -229,20 +270,75 @@ int leaf_size(const Opts& o, long long M, long long N) {
   return L;
 }
 
+// Spacing scan (Algorithm 1's Z), plus U = Z / Z_{N+1} when U_out is given.
 rs_status enqueue_uniforms(rs_handle* h, const Plan& p, bool f32, uint64_t seed, uint64_t inst, double* U_out,
                            const Opts& o, cudaStream_t st) {
-  RS_CK(h, launch_uniform_scan(f32, p.ndraw, seed, inst, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot),
-                               at<void>(h, p.o_udesc), ctr_u(h, p), h->status, o.spin, st));
-  RS_CK(h, launch_uniform_norm(f32, p.N, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot), U_out, st));
+  {
+    RS_TRACE(h, "uniform_scan", st);
+    RS_CK(h, launch_uniform_scan(f32, p.ndraw, seed, inst, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot),
+                                 at<PathConsts>(h, p.o_consts), at<void>(h, p.o_udesc), ctr_u(h, p), h->status,
+                                 o.spin, st));
+  }
+  if (U_out) {
+    RS_TRACE(h, "uniform_norm", st);
+    RS_CK(h, launch_uniform_norm(p.N, at<void>(h, p.o_Z), at<PathConsts>(h, p.o_consts), U_out, st));
+  }
+  return RS_OK;
+}
+
+rs_status enqueue_clear(rs_handle* h, const Plan& p, cudaStream_t st) {
+  RS_TRACE(h, "clear", st);
+  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  return RS_OK;
+}
+
+// Segment-prefix scan (also produces S, 1/S and, when the spacing sums exist,
+// S/Z_{N+1}).
+rs_status enqueue_prefix(rs_handle* h, const Plan& p, const Opts& o, bool f32, bool with_z, bool need_invS,
+                         cudaStream_t st) {
+  RS_TRACE(h, "seg_prefix", st);
+  const SegIndex idx = index_of(h, p);
+  RS_CK(h, launch_seg_prefix(f32, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), idx, at<void>(h, p.o_wdesc),
+                             ctr_w(h, p), at<PathConsts>(h, p.o_consts), with_z, need_invS, h->status, o.spin,
+                             o.debug & 1, st));
+  return RS_OK;
+}
+
+// Weights pass: streaming exact segment sums, then the segment-prefix scan.
+rs_status enqueue_pass1(rs_handle* h, const Plan& p, const Opts& o, bool f32, bool vec, const void* w,
+                        bool with_z, bool need_invS, cudaStream_t st) {
+  {
+    RS_TRACE(h, "w_reduce", st);
+    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), h->status, st));
+  }
+  return enqueue_prefix(h, p, o, f32, with_z, need_invS, st);
+}
+
+rs_status enqueue_write(rs_handle* h, const Plan& p, bool f32, bool vec, const void* w, double* W_out,
+                        cudaStream_t st) {
+  RS_TRACE(h, "w_write", st);
+  RS_CK(h, launch_w_write(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<PathConsts>(h, p.o_consts), W_out, st));
   return RS_OK;
 }
 
 rs_status enqueue_map(rs_handle* h, const Opts& o, const double* W, long long M, const double* U, long long N,
                       int32_t* out, cudaStream_t st) {
   switch (o.algo) {
-    case RS_MAP_BINARY: RS_CK(h, launch_map_binary(W, M, U, N, out, st)); break;
-    case RS_MAP_LINEAR: RS_CK(h, launch_map_linear(W, M, U, N, out, st)); break;
-    default: RS_CK(h, launch_map_dac(W, M, U, N, leaf_size(o, M, N), o.stage_max, out, st)); break;
+    case RS_MAP_BINARY: {
+      RS_TRACE(h, "map_binary", st);
+      RS_CK(h, launch_map_binary(W, M, U, N, out, st));
+      break;
+    }
+    case RS_MAP_LINEAR: {
+      RS_TRACE(h, "map_linear", st);
+      RS_CK(h, launch_map_linear(W, M, U, N, out, st));
+      break;
+    }
+    default: {
+      RS_TRACE(h, "map_dac", st);
+      RS_CK(h, launch_map_dac(W, M, U, N, leaf_size(o, M, N), o.stage_max, out, st));
+      break;
+    }
   }
   return RS_OK;
 }
@@ -262,10 +358,19 @@ rs_status rs_create(rs_handle** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e == cudaSuccess) e = init_log_table();
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  // the side stream carries short work that the weights pass must not starve
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (h->status) cudaFree(h->status);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
     return RS_ECUDA;
   }
@@ -275,14 +380,77 @@ rs_status rs_create(rs_handle** out) {
 
 rs_status rs_destroy(rs_handle* h) {
   if (!h) return RS_EINVAL;
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.start);
+    cudaEventDestroy(p.stop);
+  }
+  h->pending.clear();
   cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
   if (h->ws) e1 = cudaFree(h->ws);
   if (h->status) e2 = cudaFree(h->status);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
   return (e1 == cudaSuccess && e2 == cudaSuccess) ? RS_OK : RS_ECUDA;
 }
 
 const char* rs_last_error(rs_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+static void drop_pending(rs_handle* h) {
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.start);
+    cudaEventDestroy(p.stop);
+  }
+  h->pending.clear();
+}
+
+rs_status rs_trace_enable(rs_handle* h, int on) {
+  if (!h) return RS_EINVAL;
+  h->tracing = on != 0;
+  if (!on) drop_pending(h);
+  return RS_OK;
+}
+
+rs_status rs_trace_collect(rs_handle* h, int keep) {
+  if (!h) return RS_EINVAL;
+  RS_CK(h, cudaDeviceSynchronize());
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    RS_CK(h, cudaEventElapsedTime(&ms, p.start, p.stop));
+    bool found = false;
+    for (auto& t : h->totals)
+      if (std::strcmp(t.name, p.name) == 0) {
+        t.launches += 1;
+        t.ms += ms;
+        found = true;
+        break;
+      }
+    if (!found) h->totals.push_back({p.name, 1, (double)ms});
+  }
+  if (!keep) drop_pending(h);
+  return RS_OK;
+}
+
+rs_status rs_trace_report(rs_handle* h, char* buf, int64_t cap) {
+  if (!h || !buf || cap <= 0) return RS_EINVAL;
+  std::string out;
+  char line[160];
+  for (auto& t : h->totals) {
+    std::snprintf(line, sizeof(line), "%s %lld %.6f\n", t.name, t.launches, t.ms);
+    out += line;
+  }
+  const size_t n = out.size() < (size_t)(cap - 1) ? out.size() : (size_t)(cap - 1);
+  std::memcpy(buf, out.data(), n);
+  buf[n] = 0;
+  return RS_OK;
+}
+
+rs_status rs_trace_reset(rs_handle* h) {
+  if (!h) return RS_EINVAL;
+  h->totals.clear();
+  return RS_OK;
+}
 
 rs_status rs_get_status(rs_handle* h, void* stream) {
   if (!h) return RS_EINVAL;
@@ -302,6 +470,7 @@ rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t fir
   if (n < 0) return fail(h, RS_EINVAL, "n must be >= 0");
   if (n == 0) return RS_OK;
   if (!out || !aligned(out, 8)) return fail(h, RS_EINVAL, "out must be a non-NULL 8-byte aligned device pointer");
+  RS_TRACE(h, "philox", static_cast<cudaStream_t>(stream));
   RS_CK(h, launch_philox(seed, instance, first, n, reinterpret_cast<unsigned long long*>(out),
                          static_cast<cudaStream_t>(stream)));
   return RS_OK;
@@ -319,7 +488,7 @@ rs_status rs_sorted_uniform(rs_handle* h, int64_t N, uint64_t seed, uint64_t ins
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(0, N, false, true, false);
   if ((s = ensure_ws(h, p.bytes))) return s;
-  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  if ((s = enqueue_clear(h, p, st))) return s;
   return enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, U_out, o, st);
 }
 
@@ -336,12 +505,9 @@ rs_status rs_cumulative(rs_handle* h, const void* w, int64_t M, double* W_out, c
   const Plan p = make_plan(M, 0, true, false, false);
   if ((s = ensure_ws(h, p.bytes))) return s;
   const bool vec = aligned(w, 16);
-  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
-  const SegIndex idx = index_of(h, p);
-  RS_CK(h, launch_w_pass1(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_wdesc), ctr_w(h, p),
-                          at<void>(h, p.o_total), h->status, o.spin, o.debug & 1, st));
-  RS_CK(h, launch_w_write(f32, vec, w, M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_total), W_out, h->status, st));
-  return RS_OK;
+  if ((s = enqueue_clear(h, p, st))) return s;
+  if ((s = enqueue_pass1(h, p, o, f32, vec, w, false, true, st))) return s;
+  return enqueue_write(h, p, f32, vec, w, W_out, st);
 }
 
 rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
@@ -357,21 +523,32 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   if (W_out && !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be 8-byte aligned");
   if (N == 0 && !W_out) return RS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Plan p = make_plan(M, N, true, N > 0, N > 0);
+  const Plan p = make_plan(M, N, true, N > 0, false);
   if ((s = ensure_ws(h, p.bytes))) return s;
   const bool vec = aligned(w, 16);
-  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  // fork: the workspace clear and the spacing scan (independent of w) run on
+  // the handle's side stream while the weights stream through w_reduce; the
+  // prefix scan joins them (it needs Z_{N+1} and the cleared counters).
+  RS_CK(h, cudaEventRecord(h->ev_fork, st));
+  RS_CK(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  if ((s = enqueue_clear(h, p, h->side))) return s;
   if (N > 0) {
-    if ((s = enqueue_uniforms(h, p, f32, seed, instance, at<double>(h, p.o_U), o, st))) return s;
+    if ((s = enqueue_uniforms(h, p, f32, seed, instance, nullptr, o, h->side))) return s;
   }
-  const SegIndex idx = index_of(h, p);
-  RS_CK(h, launch_w_pass1(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_wdesc), ctr_w(h, p),
-                          at<void>(h, p.o_total), h->status, o.spin, o.debug & 1, st));
-  if (N > 0)
-    RS_CK(h, launch_map_seg(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<void>(h, p.o_total), at<double>(h, p.o_U),
-                            N, group_size(N), out_idx, st));
-  if (W_out)
-    RS_CK(h, launch_w_write(f32, vec, w, M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_total), W_out, h->status, st));
+  RS_CK(h, cudaEventRecord(h->ev_join, h->side));
+  {
+    RS_TRACE(h, "w_reduce", st);
+    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), h->status, st));
+  }
+  RS_CK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
+  if ((s = enqueue_prefix(h, p, o, f32, N > 0, W_out != nullptr, st))) return s;
+  if (N > 0) {
+    RS_TRACE(h, "map_seg", st);
+    const SegIndex idx = index_of(h, p);
+    RS_CK(h, launch_map_seg(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<PathConsts>(h, p.o_consts),
+                            at<void>(h, p.o_Z), N, group_size(N), out_idx, st));
+  }
+  if (W_out) return enqueue_write(h, p, f32, vec, w, W_out, st);
   return RS_OK;
 }
 
@@ -388,7 +565,7 @@ rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uin
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(0, N, false, true, true);
   if ((s = ensure_ws(h, p.bytes))) return s;
-  RS_CK(h, cudaMemsetAsync(h->ws, 0, p.clear_bytes, st));
+  if ((s = enqueue_clear(h, p, st))) return s;
   if ((s = enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, at<double>(h, p.o_U), o, st))) return s;
   return enqueue_map(h, o, W, M, at<double>(h, p.o_U), N, out_idx, st);
 }

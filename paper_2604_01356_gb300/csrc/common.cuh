@@ -124,11 +124,12 @@ __device__ __forceinline__ df neg_log_draw(uint64_t X, int p, const LogTab& T) {
   const int k = (int)((D + (1ULL << 54)) >> 55);
   // m - c = (k * 2^55 - D) * 2^-63, |.| <= 2^54: exact signed integer
   const int64_t R = (int64_t)((uint64_t)k << 55) - (int64_t)D;
-  // R as a binary32 pair scaled by 2^-63: R - Rh has at most 31 significant
-  // bits, so (Rh, Rl) holds R to 2^-48 relative.
-  const float Rh = (float)R;
-  const float Rl = (float)(R - (int64_t)Rh);
-  const df mc = {__fmul_rn(Rh, 0x1p-63f), __fmul_rn(Rl, 0x1p-63f)};
+  // R as a binary32 pair scaled by 2^-63, from two 32-bit integer conversions:
+  // R = Rh*2^30 + Rl, |Rh| <= 2^24 (exact), 0 <= Rl < 2^30 (rounded to 24
+  // bits), so the pair holds R to 2^-48 relative.
+  const int32_t Rh = (int32_t)(R >> 30);
+  const int32_t Rl = (int32_t)(R & ((1LL << 30) - 1));
+  const df mc = df_two_sum(__fmul_rn(__int2float_rn(Rh), 0x1p-33f), __fmul_rn(__int2float_rn(Rl), 0x1p-63f));
   const float2 ic = T.invc[k];
   const df r = df_mul(mc, df{ic.x, ic.y});
   // log1p(r): r - r^2/2 + r^3 (1/3 - r/4 + r^2/5 - r^3/6)
@@ -327,77 +328,305 @@ __device__ __forceinline__ double u128_to_double(u128 a) {
 }
 
 // ---------------------------------------------------------------------------
-// Exact fixed-point segment arithmetic for binary64 / binary32 weights.
-// An element of biased exponent e and integer significand m (implicit bit
-// included; e' = max(e,1)) has value m * 2^(e' - BIAS).  Inside a segment of
-// shared exponent E = max e', it becomes the integer
-//   F = round((m << SHIFT) / 2^(E - e'))           (round half up)
-// with unit 2^(E - BIAS - SHIFT).  SHIFT puts the largest element just below
-// 2^54, so 512 of them sum below 2^63: every segment sum and every
-// within-segment prefix is an exact uint64.
+// "xf": a non-negative number m * 2^e with a 128-bit integer mantissa, kept
+// normalised (top bit of m at bit 125, two bits of headroom, or m == 0).
+// All operations are integer instructions; additions truncate below 2^-125
+// of the larger operand.  Used for every prefix above the segment level, so
+// no binary64 instruction is spent per segment or per sample.
+// ---------------------------------------------------------------------------
+struct xf {
+  uint64_t lo, hi;
+  long long e;
+};
+constexpr int kXfTop = 125;
+constexpr long long kXfZeroE = -(1LL << 40);
+
+__device__ __forceinline__ int clz128(uint64_t hi, uint64_t lo) { return hi ? __clzll(hi) : 64 + __clzll(lo); }
+__device__ __forceinline__ void shl128(uint64_t& hi, uint64_t& lo, int k) {  // 0 <= k < 128
+  if (k == 0) return;
+  if (k >= 64) {
+    hi = lo << (k - 64);
+    lo = 0;
+  } else {
+    hi = (hi << k) | (lo >> (64 - k));
+    lo <<= k;
+  }
+}
+__device__ __forceinline__ void shr128(uint64_t& hi, uint64_t& lo, int k) {  // k >= 0
+  if (k == 0) return;
+  if (k >= 128) {
+    hi = lo = 0;
+  } else if (k >= 64) {
+    lo = hi >> (k - 64);
+    hi = 0;
+  } else {
+    lo = (lo >> k) | (hi << (64 - k));
+    hi >>= k;
+  }
+}
+__device__ __forceinline__ bool xf_zero(const xf& a) { return (a.hi | a.lo) == 0; }
+__device__ __forceinline__ xf xf_make(uint64_t hi, uint64_t lo, long long e) {
+  if ((hi | lo) == 0) return {0, 0, kXfZeroE};
+  const int sh = kXfTop - (127 - clz128(hi, lo));
+  if (sh > 0) shl128(hi, lo, sh);
+  else if (sh < 0) shr128(hi, lo, -sh);
+  return {lo, hi, e - sh};
+}
+__device__ __forceinline__ xf xf_from_u64(uint64_t F, long long e) { return xf_make(0, F, e); }
+// exact value of a finite non-negative binary64 (bit pattern b)
+__device__ __forceinline__ xf xf_from_f64_bits(uint64_t b) {
+  const int ex = (int)((b >> 52) & 0x7FF);
+  uint64_t m = b & 0xFFFFFFFFFFFFFULL;
+  if (ex) m |= 1ULL << 52;
+  return xf_from_u64(m, (long long)(ex ? ex : 1) - 1075);
+}
+__device__ __forceinline__ xf xf_add(xf a, xf b) {
+  if (xf_zero(a)) return b;
+  if (xf_zero(b)) return a;
+  if (a.e < b.e) {
+    const xf t = a;
+    a = b;
+    b = t;
+  }
+  const long long d = a.e - b.e;
+  uint64_t bh = b.hi, bl = b.lo;
+  shr128(bh, bl, d > 127 ? 128 : (int)d);
+  uint64_t lo = a.lo + bl;
+  uint64_t hi = a.hi + bh + (lo < a.lo ? 1ULL : 0ULL);
+  long long e = a.e;
+  if (hi >> 62) {  // top bit reached 126
+    shr128(hi, lo, 1);
+    ++e;
+  }
+  return {lo, hi, e};
+}
+// a - b for a >= b
+__device__ __forceinline__ xf xf_sub(xf a, xf b) {
+  if (xf_zero(b)) return a;
+  const long long d = a.e - b.e;
+  if (d < 0) return {0, 0, kXfZeroE};
+  uint64_t bh = b.hi, bl = b.lo;
+  shr128(bh, bl, d > 127 ? 128 : (int)d);
+  if (bh > a.hi || (bh == a.hi && bl > a.lo)) return {0, 0, kXfZeroE};
+  const uint64_t lo = a.lo - bl;
+  const uint64_t hi = a.hi - bh - (a.lo < bl ? 1ULL : 0ULL);
+  return xf_make(hi, lo, a.e);
+}
+__device__ __forceinline__ bool xf_lt(const xf& a, const xf& b) {
+  if (xf_zero(a)) return !xf_zero(b);
+  if (xf_zero(b)) return false;
+  if (a.e != b.e) return a.e < b.e;
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool xf_le(const xf& a, const xf& b) { return !xf_lt(b, a); }
+
+// 64x64 -> 128
+__device__ __forceinline__ void mul64(uint64_t a, uint64_t b, uint64_t& hi, uint64_t& lo) {
+  lo = a * b;
+  hi = __umul64hi(a, b);
+}
+// Product of two normalised xf (top 128 bits of the 256-bit mantissa product).
+__device__ __forceinline__ xf xf_mul(const xf& a, const xf& b) {
+  if (xf_zero(a) || xf_zero(b)) return {0, 0, kXfZeroE};
+  uint64_t p0h, p0l, p1h, p1l, p2h, p2l, p3h, p3l;
+  mul64(a.lo, b.lo, p0h, p0l);
+  mul64(a.lo, b.hi, p1h, p1l);
+  mul64(a.hi, b.lo, p2h, p2l);
+  mul64(a.hi, b.hi, p3h, p3l);
+  // r = p3<<128 + (p1+p2)<<64 + p0, as words r3 r2 r1 (r0 dropped)
+  uint64_t r1 = p0h + p1l;
+  uint64_t c1 = r1 < p0h;
+  r1 += p2l;
+  c1 += r1 < p2l;
+  uint64_t r2 = p3l + p1h;
+  uint64_t c2 = r2 < p3l;
+  r2 += p2h;
+  c2 += r2 < p2h;
+  r2 += c1;
+  c2 += r2 < c1;
+  const uint64_t r3 = p3h + c2;
+  // product < 2^252: keep bits 126..253
+  const uint64_t hi = (r3 << 2) | (r2 >> 62);
+  const uint64_t lo = (r2 << 2) | (r1 >> 62);
+  return xf_make(hi, lo, a.e + b.e + 126);
+}
+// xf times an unsigned 64-bit integer (truncated to 128 significant bits).
+__device__ __forceinline__ xf xf_mul_u64(const xf& a, uint64_t F) {
+  if (xf_zero(a) || F == 0) return {0, 0, kXfZeroE};
+  uint64_t ph, pl, qh, ql;
+  mul64(a.lo, F, ph, pl);
+  mul64(a.hi, F, qh, ql);
+  // 192-bit product: w2 w1 w0 = (qh, ql + ph, pl)
+  uint64_t w1 = ql + ph;
+  const uint64_t w2 = qh + (w1 < ql ? 1ULL : 0ULL);
+  // keep the top 128 bits below the leading bit of w2:w1:w0
+  const int lz = w2 ? __clzll(w2) : 64 + __clzll(w1);
+  uint64_t hi, lo;
+  long long e = a.e;
+  if (lz >= 64) {  // w2 == 0: the product fits in w1:w0
+    hi = w1;
+    lo = pl;
+  } else {  // keep bits (64-lz) .. (191-lz) of the product
+    hi = (w2 << lz) | (lz ? (w1 >> (64 - lz)) : 0);
+    lo = (w1 << lz) | (lz ? (pl >> (64 - lz)) : 0);
+    e += 64 - lz;
+  }
+  return xf_make(hi, lo, e);
+}
+// xf times an unsigned 128-bit integer.
+__device__ __forceinline__ xf xf_mul_u128(const xf& a, u128 z) {
+  return xf_mul(a, xf_make(z.hi, z.lo, 0));
+}
+
+// Bit pattern of the binary64 nearest to x (round half to even).
+__device__ __forceinline__ uint64_t xf_to_f64_bits(const xf& x) {
+  if (xf_zero(x)) return 0;
+  long long be = x.e + kXfTop + 1023;  // biased exponent of the leading bit
+  int drop = 73;                        // bits below the 53-bit significand
+  if (be < 1) {                         // subnormal result
+    drop += (int)(1 - be);
+    be = 0;
+    if (drop >= 128) return 0;
+  }
+  uint64_t mh = x.hi, ml = x.lo;
+  shr128(mh, ml, drop);                 // kept significand (fits in 64 bits)
+  uint64_t rh = x.hi, rl = x.lo;        // dropped part
+  uint64_t kh = mh, kl = ml;
+  shl128(kh, kl, drop);
+  rl = x.lo - kl;
+  rh = x.hi - kh - (x.lo < kl ? 1ULL : 0ULL);
+  uint64_t half_h = 0, half_l = 0;
+  if (drop - 1 >= 64) half_h = 1ULL << (drop - 1 - 64);
+  else half_l = 1ULL << (drop - 1);
+  uint64_t m = ml;
+  const bool gt = rh > half_h || (rh == half_h && rl > half_l);
+  const bool eq = rh == half_h && rl == half_l;
+  if (gt || (eq && (m & 1))) ++m;
+  if (be == 0) {
+    return m;  // subnormal (a carry into bit 52 correctly yields the smallest normal)
+  }
+  if (m >> 53) {
+    m >>= 1;
+    ++be;
+  }
+  if (be >= 2047) return 0x7FF0000000000000ULL;
+  return ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFULL);
+}
+
+// Search key of x: the bit pattern of x truncated to binary64 (a monotone
+// map; values below the binary64 normal range all map to 0).  Cheap: no
+// rounding logic.
+__device__ __forceinline__ unsigned long long xf_key(const xf& x) {
+  if (xf_zero(x)) return 0ULL;
+  const long long be = x.e + kXfTop + 1023;
+  if (be < 1) return 0ULL;
+  if (be >= 2047) return 0x7FF0000000000000ULL;
+  return ((unsigned long long)be << 52) | ((x.hi >> 9) & 0xFFFFFFFFFFFFFULL);
+}
+
+// x as a binary64 pair (hi nearest, lo = nearest of the signed remainder).
+__device__ __forceinline__ dd xf_to_dd(const xf& x) {
+  const uint64_t hb = xf_to_f64_bits(x);
+  const double hi = __longlong_as_double((long long)hb);
+  const xf h = xf_from_f64_bits(hb);
+  if (xf_lt(x, h)) {
+    const xf r = xf_sub(h, x);
+    return {hi, -__longlong_as_double((long long)xf_to_f64_bits(r))};
+  }
+  const xf r = xf_sub(x, h);
+  return {hi, __longlong_as_double((long long)xf_to_f64_bits(r))};
+}
+// a / b for normalised non-zero xf, on one thread: the mantissas are divided
+// as binary64 pairs scaled to [1, 2) (so nothing over- or underflows) and the
+// exponent difference is carried in the integer exponent.
+__device__ __forceinline__ xf xf_from_dd(dd v);
+__device__ __forceinline__ xf xf_div(const xf& a, const xf& b) {
+  if (xf_zero(a) || xf_zero(b)) return {0, 0, kXfZeroE};
+  const dd ad = xf_to_dd(xf{a.lo, a.hi, -kXfTop});
+  const dd bd = xf_to_dd(xf{b.lo, b.hi, -kXfTop});
+  xf q = xf_from_dd(dd_div(ad, bd));
+  q.e += a.e - b.e;
+  return q;
+}
+
+// positive binary64 pair to xf (hi > 0, |lo| <= ulp(hi)/2)
+__device__ __forceinline__ xf xf_from_dd(dd v) {
+  const xf h = xf_from_f64_bits((uint64_t)__double_as_longlong(v.hi));
+  if (v.lo >= 0.0) return xf_add(h, xf_from_f64_bits((uint64_t)__double_as_longlong(v.lo)));
+  return xf_sub(h, xf_from_f64_bits((uint64_t)__double_as_longlong(-v.lo)));
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point segment arithmetic for binary64 / binary32 weights.
+// An element with exponent field t and significand m (implicit bit included,
+// e' = max(t,1)) has value m * 2^(e' - kBias).  Inside a segment of shared
+// exponent E = max e' it becomes the integer
+//   F = floor((m << kShift) / 2^(E - e'))        (truncating grid)
+// with unit 2^(E - kBias - kShift).  The largest element keeps every bit and
+// 512 elements sum below 2^63, so every segment sum and every within-segment
+// prefix is an exact uint64.  Invalid elements (negative, NaN, infinity) have
+// t >= 0x7FF (the sign bit lands in t), so E - e' wraps to a huge shift and
+// they contribute 0 without a branch; they are reported separately.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FixedTraits;
 template <>
 struct FixedTraits<double> {
   using Bits = uint64_t;
-  static constexpr int kBias = 1075;  // value = m * 2^(e' - 1075)
-  static constexpr int kShift = 1;    // m < 2^53 -> m<<1 < 2^54
-  __device__ static __forceinline__ Bits bits(double x) { return (Bits)__double_as_longlong(x); }
-  __device__ static __forceinline__ int expo(Bits b) { return (int)((b >> 52) & 0x7FF); }
-  __device__ static __forceinline__ uint64_t signif(Bits b) {
-    const uint64_t f = b & 0xFFFFFFFFFFFFFULL;
-    return ((b >> 52) & 0x7FF) ? (f | (1ULL << 52)) : f;
-  }
-  // invalid: negative non-zero, NaN or infinity
+  static constexpr int kBias = 1075;
+  static constexpr int kShift = 0;  // m < 2^53: 512 of them stay below 2^62
+  __device__ static __forceinline__ uint32_t top(Bits b) { return (uint32_t)(b >> 52); }  // sign + exponent
+  __device__ static __forceinline__ uint32_t valid_top(Bits b) { return (uint32_t)(b >> 52) < 0x7FFu; }
+  // precise invalidity (negative non-zero, NaN, infinity); -0.0 is a valid zero
   __device__ static __forceinline__ bool bad(Bits b) {
     return ((b >> 52) & 0x7FF) == 0x7FF || ((b >> 63) && (b << 1) != 0);
   }
+  __device__ static __forceinline__ uint64_t fixed(Bits b, uint32_t E) {
+    const uint32_t t = top(b);
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFULL) | (t ? (1ULL << 52) : 0ULL);
+    uint32_t d = E - (t > 1u ? t : 1u);
+    d = d > 63u ? 63u : d;
+    return m >> d;
+  }
+  __device__ static __forceinline__ double value(Bits b) { return __longlong_as_double((long long)b); }
 };
 template <>
 struct FixedTraits<float> {
   using Bits = uint32_t;
   static constexpr int kBias = 150;
   static constexpr int kShift = 30;  // m < 2^24 -> m<<30 < 2^54
-  __device__ static __forceinline__ Bits bits(float x) { return (Bits)__float_as_uint(x); }
-  __device__ static __forceinline__ int expo(Bits b) { return (int)((b >> 23) & 0xFF); }
-  __device__ static __forceinline__ uint64_t signif(Bits b) {
-    const uint32_t f = b & 0x7FFFFFu;
-    return ((b >> 23) & 0xFF) ? (uint64_t)(f | (1u << 23)) : (uint64_t)f;
-  }
+  __device__ static __forceinline__ uint32_t top(Bits b) { return b >> 23; }
+  __device__ static __forceinline__ uint32_t valid_top(Bits b) { return (b >> 23) < 0xFFu; }
   __device__ static __forceinline__ bool bad(Bits b) { return ((b >> 23) & 0xFF) == 0xFF || ((b >> 31) && (b << 1) != 0); }
+  __device__ static __forceinline__ uint64_t fixed(Bits b, uint32_t E) {
+    const uint32_t t = top(b);
+    const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | (t ? 0x800000u : 0u)) << 30;
+    uint32_t d = E - (t > 1u ? t : 1u);
+    d = d > 63u ? 63u : d;
+    return m >> d;
+  }
 };
+
+// Segment exponent candidate of one element: its exponent field when it is a
+// valid non-negative finite number, else 0 (max with 1 is applied later).
+template <typename T>
+__device__ __forceinline__ uint32_t seg_top(typename FixedTraits<T>::Bits b) {
+  using Tr = FixedTraits<T>;
+  const uint32_t t = Tr::top(b);
+  return t < (sizeof(T) == 8 ? 0x7FFu : 0xFFu) ? t : 0u;
+}
+template <typename T>
+__device__ __forceinline__ uint64_t to_fixed(typename FixedTraits<T>::Bits b, int E) {
+  return FixedTraits<T>::fixed(b, (uint32_t)E);
+}
 
 // A segment is a "head" segment when everything before it is too small for
 // the segment grid to keep 1e-12 relative accuracy on the prefixes inside it:
-// the within-segment rounding is at most 256 units, so P_s >= 2^50 units is
-// enough.  Head segments of binary64 weights are resolved with binary64-pair
-// prefixes instead (only the first segment for ordinary weights).
-__device__ __forceinline__ bool head_segment(double P_hi, int E, int bias_shift) {
-  return P_hi < scalbn(1.0, E - bias_shift + 50);
-}
-
-// e' used for the segment exponent: 0 for zeros and invalid elements (they
-// contribute nothing), max(e,1) otherwise.
-template <typename T>
-__device__ __forceinline__ int seg_expo(typename FixedTraits<T>::Bits b) {
-  using Tr = FixedTraits<T>;
-  if (Tr::bad(b)) return 0;
-  const int e = Tr::expo(b);
-  const uint64_t m = Tr::signif(b);
-  return m ? (e > 1 ? e : 1) : 0;
-}
-
-template <typename T>
-__device__ __forceinline__ uint64_t to_fixed(typename FixedTraits<T>::Bits b, int E) {
-  using Tr = FixedTraits<T>;
-  if (Tr::bad(b)) return 0;
-  const uint64_t m = Tr::signif(b) << Tr::kShift;
-  const int e = Tr::expo(b);
-  const int d = E - (e > 1 ? e : 1);
-  if (d <= 0) return m;  // d == 0 (E is the max exponent)
-  if (d >= 56) return 0;
-  return (m + (1ULL << (d - 1))) >> d;
+// the within-segment truncation is below 512 units, so P_s >= 2^50 units is
+// enough.  Head segments of binary64 weights are resolved with exact
+// per-element prefixes instead (only the first segment for ordinary weights).
+__device__ __forceinline__ bool head_segment(const xf& P, int E, int bias_shift) {
+  return xf_zero(P) || P.e + kXfTop < (long long)(E - bias_shift + 50);
 }
 
 // ---------------------------------------------------------------------------
@@ -459,12 +688,15 @@ __device__ __forceinline__ V ld_cg(const V* p) {
 // Add for the value types used in look-back.
 __device__ __forceinline__ dd lb_add(dd a, dd b) { return dd_add(a, b); }
 __device__ __forceinline__ u128 lb_add(u128 a, u128 b) { return u128_add(a, b); }
+__device__ __forceinline__ xf lb_add(xf a, xf b) { return xf_add(a, b); }
 template <typename V>
 __device__ __forceinline__ V lb_zero();
 template <>
 __device__ __forceinline__ dd lb_zero<dd>() { return {0.0, 0.0}; }
 template <>
 __device__ __forceinline__ u128 lb_zero<u128>() { return {0ULL, 0ULL}; }
+template <>
+__device__ __forceinline__ xf lb_zero<xf>() { return {0ULL, 0ULL, kXfZeroE}; }
 
 template <typename V>
 __device__ __forceinline__ V shfl_v(V v, int src) {

@@ -66,158 +66,248 @@ __device__ __forceinline__ void load_blocked(const T* __restrict__ w, long long 
   }
 }
 
-__device__ __forceinline__ dd seg_P(const SegRec* seg, long long s) { return dd{seg[s].P_hi, seg[s].P_lo}; }
-
-// Last segment s with P_s < key (binary64-pair comparison).  A 32-ary search
-// on the hi parts down the index, then an exact fix-up on (hi, lo).
-__device__ __forceinline__ long long locate_segment(const SegRec* __restrict__ seg, const SegIndex& idx, dd key,
-                                                    int lane) {
-  const unsigned long long kb = (unsigned long long)__double_as_longlong(key.hi);
-  long long c = 0;
-  for (int l = idx.nlev - 1; l >= 0; --l) {
-    const long long j = c * 32 + lane;
-    const unsigned long long e = j < idx.lvl_n[l] ? __ldcg(idx.lvl[l] + j) : ~0ULL;
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, e < kb);
-    const int cnt = __popc(bal);
-    c = c * 32 + (cnt > 0 ? cnt - 1 : 0);
-  }
-  long long s = c;
-  int guard = 0;
-  while (s + 1 < idx.nseg && dd_lt(seg_P(seg, s + 1), key) && ++guard < 4096) ++s;
-  while (s > 0 && dd_le(key, seg_P(seg, s)) && ++guard < 8192) --s;
-  return s;
+__device__ __forceinline__ xf rec_P(const SegRec* __restrict__ seg, long long s) {
+  return {__ldcg(&seg[s].Pm_lo), __ldcg(&seg[s].Pm_hi), (long long)__ldcg((const unsigned long long*)&seg[s].Pe)};
+}
+__device__ __forceinline__ xf ld_consts_xf(const unsigned long long* p) {
+  return {__ldcg(p), __ldcg(p + 1), (long long)__ldcg(p + 2)};
 }
 
-// Head segment of binary64 weights: count the elements whose binary64-pair
-// cumulative value P_s + sum_{k<=j} w_k is still below key.
+// Last segment s with P_s < key: a 32-ary search down the index on the
+// binary64 keys (rounding is monotone, so it can only stop early on ties),
+// then an exact forward / backward fix-up on the 128-bit values.
+__device__ __forceinline__ long long fixup_segment(const SegRec* __restrict__ seg, long long nseg, long long s,
+                                                   const xf& key) {
+  int guard = 0;
+  while (s + 1 < nseg && xf_lt(rec_P(seg, s + 1), key) && ++guard < 4096) ++s;
+  while (s > 0 && xf_le(key, rec_P(seg, s)) && ++guard < 8192) --s;
+  return s;
+}
+// Level-0 step shared by both searches: within the 32 segments of node c,
+// the last one whose key is below kb; exact fix-up only on ties or at the
+// window's edge (key(P_s) < kb < key(P_{s+1}) strictly proves
+// P_s < key <= P_{s+1}, since truncation to binary64 is monotone).
+__device__ __forceinline__ long long level0_step(const SegRec* __restrict__ seg, const SegIndex& idx, long long c,
+                                                 unsigned long long kb, const xf& key, int lane) {
+  const long long j = c * 32 + lane;
+  const unsigned long long e = j < idx.lvl_n[0] ? __ldcg(idx.lvl[0] + j) : ~0ULL;
+  const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
+  const long long s = c * 32 + (cnt > 0 ? cnt - 1 : 0);
+  const unsigned long long next = __shfl_sync(0xFFFFFFFFu, e, cnt & 31);
+  if (cnt > 0 && cnt < 32 && next != kb) return s;
+  return fixup_segment(seg, idx.nseg, s, key);
+}
+
+// Last segment s with P_s < key: 32-ary descent of the index in global
+// memory (general case).
+__device__ __forceinline__ long long locate_segment(const SegRec* __restrict__ seg, const SegIndex& idx,
+                                                    unsigned long long kb, const xf& key, int lane) {
+  long long c = 0;
+  for (int l = idx.nlev - 1; l >= 1; --l) {
+    const long long j = c * 32 + lane;
+    const unsigned long long e = j < idx.lvl_n[l] ? __ldcg(idx.lvl[l] + j) : ~0ULL;
+    const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
+    c = c * 32 + (cnt > 0 ? cnt - 1 : 0);
+  }
+  return level0_step(seg, idx, c, kb, key, lane);
+}
+
+// Same with level 1 of the index staged in shared memory (binary search there,
+// then one global level-0 window).
+__device__ __forceinline__ long long locate_segment_smem(const SegRec* __restrict__ seg, const SegIndex& idx,
+                                                         const unsigned long long* __restrict__ top, int ntop,
+                                                         unsigned long long kb, const xf& key, int lane) {
+  int lo = 0, hi = ntop;  // first entry >= kb
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (top[m] < kb) lo = m + 1;
+    else hi = m;
+  }
+  return level0_step(seg, idx, lo > 0 ? lo - 1 : 0, kb, key, lane);
+}
+
+// Head segment of binary64 weights: number of elements j with
+// sum_{k<=j} w_k < rem, rem = key - P_s.  The weights are put on a 128-bit
+// grid scaled to rem (unit 2^(rem.e + 25), so rem is about 2^100 units) and
+// summed with saturation at 2^102: the decision is exact up to 512 units,
+// i.e. 2^-91 of rem, whatever the dynamic range of the segment.
+__device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
+  const u128 s = u128_add(a, b);
+  return (s.hi >> 38) ? u128{0ULL, 1ULL << 38} : s;  // cap at 2^102
+}
+// One binary64 weight in units of 2^ue (saturated at 2^102).
+__device__ __forceinline__ u128 head_val(uint64_t b, long long ue) {
+  const uint32_t t = (uint32_t)(b >> 52);
+  if (t >= 0x7FFu) return u128{0ULL, 0ULL};
+  const uint64_t m = (b & 0xFFFFFFFFFFFFFULL) | (t ? (1ULL << 52) : 0ULL);
+  const long long sh = (long long)(t > 1u ? t : 1u) - 1075 - ue;
+  if (sh >= 50) return u128{0ULL, m ? (1ULL << 38) : 0ULL};
+  if (sh >= 0) {
+    uint64_t vh = 0, vl = m;
+    shl128(vh, vl, (int)sh);
+    return u128{vl, vh};
+  }
+  return sh > -64 ? u128{m >> (-sh), 0ULL} : u128{0ULL, 0ULL};
+}
 template <bool kVec>
-__device__ __forceinline__ int head_count(const double* __restrict__ w, long long base, long long M, dd Ps, dd key,
-                                       int lane) {
+__device__ __forceinline__ int head_count(const double* __restrict__ w, long long base, long long M, const xf& Ps,
+                                          const xf& key, int lane) {
   using Tr = FixedTraits<double>;
+  const xf rem = xf_sub(key, Ps);
+  if (xf_zero(rem)) return 0;
+  // R = rem / unit = rem.m >> 25, in [2^100, 2^101)
+  uint64_t rh = rem.hi, rl = rem.lo;
+  shr128(rh, rl, 25);
+  const long long ue = rem.e + 25;
   Tr::Bits b[kSegV];
   load_blocked<double, kVec>(w, base, M, lane, b);
-  dd run = {0.0, 0.0};
+  u128 run = {0ULL, 0ULL};
 #pragma unroll
-  for (int i = 0; i < kSegV; ++i) run = dd_add_d(run, Tr::bad(b[i]) ? 0.0 : __longlong_as_double((long long)b[i]));
-  dd x = warp_incl_scan_v(run, lane);
-  x = dd_add(dd_add(x, dd{-run.hi, -run.lo}), Ps);
+  for (int i = 0; i < kSegV; ++i) run = sat_add(run, head_val(b[i], ue));
+  // exclusive offset of this lane (saturating warp scan)
+  u128 incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u128 t = shfl_up_v(incl, o);
+    if (lane >= o) incl = sat_add(t, incl);
+  }
+  u128 x = shfl_up_v(incl, 1);
+  if (lane == 0) x = u128{0ULL, 0ULL};
   int cnt = 0;
 #pragma unroll
   for (int i = 0; i < kSegV; ++i) {
-    x = dd_add_d(x, Tr::bad(b[i]) ? 0.0 : __longlong_as_double((long long)b[i]));
-    cnt += dd_lt(x, key) ? 1 : 0;
+    x = sat_add(x, head_val(b[i], ue));
+    cnt += (x.hi < rh || (x.hi == rh && x.lo < rl)) ? 1 : 0;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
   return cnt;
 }
 template <bool kVec>
-__device__ __forceinline__ int head_count(const float*, long long, long long, dd, dd, int) {
+__device__ __forceinline__ int head_count(const float*, long long, long long, const xf&, const xf&, int) {
   return 0;  // binary32 weights never need it: their grid is finer than the tolerance
 }
 
+// K = ceil(rem / 2^ue) clamped to [1, F] (rem is a normalised xf).
+__device__ __forceinline__ unsigned long long ceil_units(const xf& rem, long long ue, unsigned long long F) {
+  if (xf_zero(rem)) return 1;
+  const long long sh = rem.e - ue;
+  unsigned long long K;
+  if (sh >= 0) {
+    K = F;  // rem >= 2^125 units
+  } else if (sh <= -128) {
+    K = 1;
+  } else {
+    const int r = (int)(-sh);
+    uint64_t hi = rem.hi, lo = rem.lo;
+    // add 2^r - 1, then shift right by r
+    uint64_t ah = 0, al = 0;
+    if (r >= 64) {
+      ah = (r == 64) ? 0 : ((1ULL << (r - 64)) - 1);
+      al = ~0ULL;
+    } else {
+      al = (1ULL << r) - 1;
+    }
+    uint64_t nl = lo + al;
+    uint64_t nh = hi + ah + (nl < lo ? 1ULL : 0ULL);
+    shr128(nh, nl, r);
+    K = nh ? F : nl;
+  }
+  if (K > F) K = F;
+  if (K < 1) K = 1;
+  return K;
+}
+
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, long long M, const SegRec* __restrict__ seg,
-                                                 SegIndex idx, const dd* __restrict__ total,
-                                                 const double* __restrict__ U, long long N, int G,
-                                                 int* __restrict__ out) {
+__global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, long long M,
+                                                    const SegRec* __restrict__ seg, SegIndex idx,
+                                                    const PathConsts* __restrict__ consts,
+                                                    const u128* __restrict__ Z, long long N, int G, int ntop,
+                                                    int* __restrict__ out) {
   using Tr = FixedTraits<T>;
   using Bits = typename Tr::Bits;
+  constexpr int kBS = Tr::kBias + Tr::kShift;
+  extern __shared__ unsigned long long s_top[];  // level 1 of the index when ntop > 0
+  __shared__ xf s_c, s_S;
+  const long long gw0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // the first sample's spacing sum is fetched while the index is staged
+  u128 z_first = {0ULL, 0ULL};
+  if (gw0 * (long long)G < N) z_first = Z[gw0 * (long long)G];
+  for (int t = threadIdx.x; t < ntop; t += blockDim.x) s_top[t] = __ldcg(idx.lvl[1] + t);
+  if (threadIdx.x == 0) {
+    s_c = ld_consts_xf(consts->c);
+    s_S = ld_consts_xf(consts->S);
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long nseg = idx.nseg;
-  const dd S = *total;
   for (long long g = gw; g * (long long)G < N; g += nw) {
     const long long i0 = g * (long long)G;
     const long long i1 = (i0 + G < N) ? i0 + G : N;
-    long long s = -1;     // segment held in registers
-    dd Ps = {0, 0}, Pn = {0, 0};
+    long long s = -1;  // segment held in registers
+    xf Ps = lb_zero<xf>(), Pn = lb_zero<xf>();
     int E = 1, len = 0;
     bool head = false;
     unsigned long long F = 0;
     uint64_t pref[kSegV];
 #pragma unroll
-    for (int i = 0; i < kSegV; ++i) pref[i] = 0;
+    for (int q = 0; q < kSegV; ++q) pref[q] = 0;
     for (long long i = i0; i < i1; ++i) {
-      dd key = {0.0, 0.0};
-      if (lane == 0) key = dd_mul(dd{__ldg(U + i), 0.0}, S);
-      key = shfl_v(key, 0);
-      if (s < 0 || !(dd_lt(Ps, key) && dd_le(key, Pn))) {
+      const u128 z = (g == gw0 && i == i0) ? z_first : Z[i];
+      // key = U_i * S = Z_i * (S / Z_{N+1}): exact integer product
+      const xf key = xf_mul_u128(s_c, z);
+      if (s < 0 || !(xf_lt(Ps, key) && xf_le(key, Pn))) {
+        const unsigned long long kb = xf_key(key);
         long long ns = -1;
-        if (s >= 0 && dd_lt(Pn, key)) {
+        if (s >= 0 && xf_lt(Pn, key)) {
           // forward skip over the next 32 segments (merge walk)
           const long long j = s + 1 + lane;
-          const unsigned long long kb = (unsigned long long)__double_as_longlong(key.hi);
           const unsigned long long e = j < nseg ? __ldcg(idx.lvl[0] + j) : ~0ULL;
-          const unsigned bal = __ballot_sync(0xFFFFFFFFu, e < kb);
-          const int cnt = __popc(bal);
-          if (cnt < 32) {
-            ns = s + cnt;
-            int guard = 0;
-            while (ns + 1 < nseg && dd_lt(seg_P(seg, ns + 1), key) && ++guard < 4096) ++ns;
-            while (ns > 0 && dd_le(key, seg_P(seg, ns)) && ++guard < 8192) --ns;
-          }
+          const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
+          if (cnt < 32) ns = fixup_segment(seg, nseg, s + cnt, key);
         }
-        if (ns < 0) ns = locate_segment(seg, idx, key, lane);
+        if (ns < 0)
+          ns = ntop > 0 ? locate_segment_smem(seg, idx, s_top, ntop, kb, key, lane)
+                        : locate_segment(seg, idx, kb, key, lane);
         s = ns;
+        // record, next prefix and the segment's weights are independent loads
+        Bits b[kSegV];
+        load_blocked<T, kVec>(w, s * kSeg, M, lane, b);
         const SegRec r = seg[s];
-        Ps = dd{r.P_hi, r.P_lo};
-        Pn = (s + 1 < nseg) ? seg_P(seg, s + 1) : S;
+        Pn = (s + 1 < nseg) ? rec_P(seg, s + 1) : s_S;
+        Ps = xf{r.Pm_lo, r.Pm_hi, r.Pe};
         E = r.E;
         len = r.len;
         F = r.F;
-        head = sizeof(T) == 8 && head_segment(r.P_hi, E, Tr::kBias + Tr::kShift);
-        Bits b[kSegV];
-        load_blocked<T, kVec>(w, s * kSeg, M, lane, b);
-        uint64_t run = 0;
+        head = sizeof(T) == 8 && head_segment(Ps, E, kBS);
+        if (!head) {
+          uint64_t run = 0;
 #pragma unroll
-        for (int q = 0; q < kSegV; ++q) {
-          run += to_fixed<T>(b[q], E);
-          pref[q] = run;
+          for (int q = 0; q < kSegV; ++q) {
+            run += Tr::fixed(b[q], (uint32_t)E);
+            pref[q] = run;
+          }
+          const uint64_t off = warp_incl_scan_u64(run, lane) - run;
+#pragma unroll
+          for (int q = 0; q < kSegV; ++q) pref[q] += off;
         }
-        const uint64_t incl = warp_incl_scan_u64(run, lane);
-        const uint64_t off = incl - run;
-#pragma unroll
-        for (int q = 0; q < kSegV; ++q) pref[q] += off;
       }
+      int cnt;
       if (head) {
-        const int hc = head_count<kVec>(w, s * kSeg, M, Ps, key, lane);
-        if (lane == 0) {
-          long long j = hc < len ? hc : len - 1;
-          long long r = s * kSeg + j;
-          if (r > M - 1) r = M - 1;
-          out[i] = (int)r;
-        }
-        continue;
-      }
-      // K = ceil((key - P_s) / unit): the first element whose exact prefix
-      // reaches K is the answer.  Clamped to [1, F].
-      unsigned long long K = 1;
-      if (lane == 0) {
-        const dd rem = dd_sub(key, Ps);
-        const int sc = Tr::kBias + Tr::kShift - E;
-        const double th = ldexp2(rem.hi, sc), tl = ldexp2(rem.lo, sc);
-        if (!(th > 0.0)) {
-          K = 1;
-        } else if (th >= 9.2e18) {
-          K = F;
-        } else {
-          const double c = ceil(th);
-          if (c != th) K = (unsigned long long)c;
-          else K = (unsigned long long)th + (unsigned long long)(long long)ceil(tl);
-        }
-        if (K > F) K = F;
-        if (K < 1) K = 1;
-      }
-      K = __shfl_sync(0xFFFFFFFFu, K, 0);
-      int cnt = 0;
+        cnt = head_count<kVec>(w, s * kSeg, M, Ps, key, lane);
+      } else {
+        // first element whose exact prefix reaches K = ceil((key - P_s)/unit)
+        const unsigned long long K = ceil_units(xf_sub(key, Ps), (long long)(E - kBS), F);
+        cnt = 0;
 #pragma unroll
-      for (int q = 0; q < kSegV; ++q) cnt += pref[q] < K ? 1 : 0;
+        for (int q = 0; q < kSegV; ++q) cnt += pref[q] < K ? 1 : 0;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+      }
       if (lane == 0) {
-        long long j = cnt < len ? cnt : len - 1;
+        const long long j = cnt < len ? cnt : len - 1;
         long long r = s * kSeg + j;
         if (r > M - 1) r = M - 1;
         out[i] = (int)r;
@@ -226,25 +316,32 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
   }
 }
 
+constexpr int kMapTopMax = 6144;  // entries (48 KB, the default dynamic shared-memory limit)
+
 template <typename T, bool kVec>
-static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, const SegIndex& idx, const void* total,
-                             const double* U, long long N, int G, int* out, cudaStream_t st) {
+static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, const SegIndex& idx,
+                             const PathConsts* consts, const void* Z, long long N, int G, int* out, cudaStream_t st) {
   const long long groups = (N + G - 1) / G;
   long long blocks = (groups + 7) / 8;
   const long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k_map_seg<T, kVec><<<(unsigned)blocks, 256, 0, st>>>((const T*)w, M, seg, idx, (const dd*)total, U, N, G, out);
+  // stage level 1 of the segment index in shared memory when it is small
+  int ntop = 0;
+  if (idx.nlev >= 2 && idx.lvl_n[1] <= kMapTopMax) ntop = (int)idx.lvl_n[1];
+  const size_t smem = (size_t)ntop * sizeof(unsigned long long);
+  k_map_seg<T, kVec><<<(unsigned)blocks, 256, smem, st>>>((const T*)w, M, seg, idx, consts, (const u128*)Z, N, G, ntop,
+                                                          out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegIndex& idx,
-                           const void* total, const double* U, long long N, int G, int* out, cudaStream_t st) {
+                           const PathConsts* consts, const void* Z, long long N, int G, int* out, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  if (f32) return vec ? map_seg_t<float, true>(w, M, seg, idx, total, U, N, G, out, st)
-                      : map_seg_t<float, false>(w, M, seg, idx, total, U, N, G, out, st);
-  return vec ? map_seg_t<double, true>(w, M, seg, idx, total, U, N, G, out, st)
-             : map_seg_t<double, false>(w, M, seg, idx, total, U, N, G, out, st);
+  if (f32) return vec ? map_seg_t<float, true>(w, M, seg, idx, consts, Z, N, G, out, st)
+                      : map_seg_t<float, false>(w, M, seg, idx, consts, Z, N, G, out, st);
+  return vec ? map_seg_t<double, true>(w, M, seg, idx, consts, Z, N, G, out, st)
+             : map_seg_t<double, false>(w, M, seg, idx, consts, Z, N, G, out, st);
 }
 
 // ---------------------------------------------------------------------------

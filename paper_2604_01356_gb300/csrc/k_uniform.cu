@@ -2,13 +2,14 @@
 //   z_k = -log(v_k), k = 1..N+1;  Z_i = sum_{k<=i} z_k;  U_i = Z_i / Z_{N+1}.
 // (The printed normaliser Z_{i+1} is read as Z_{N+1}.)
 //
-// GB300 form.  One pass over the N+1 draws: each lane draws 16 consecutive
-// Philox words, evaluates the spacings (binary32-pair log for binary64 draws,
-// binary32 logf for binary32 draws), converts them EXACTLY to integers on a
-// 2^-88 grid and scans them as unsigned 128-bit integers; tiles of 4096 draws
-// chain their sums by decoupled look-back.  Integer sums make Z exact,
-// monotone and independent of scheduling.  A second small kernel forms
-// U_i = fl(Z_i) * fl(1/Z_{N+1}) (monotone in Z_i by construction).
+// GB300 form.  One pass over the N+1 draws: each thread takes one draw,
+// evaluates the spacing (binary32-pair log for binary64 draws, binary32 logf
+// for binary32 draws), converts it EXACTLY to an integer on a 2^-88 grid and
+// the block scans them as unsigned 128-bit integers; tiles of 256 draws chain
+// their sums by decoupled look-back.  Integer sums make Z
+// exact, monotone and independent of scheduling.  The resampling map consumes
+// Z directly; when U itself is wanted a second kernel rounds Z_i / Z_{N+1}
+// to binary64 (monotone in Z_i by construction).
 #include <cmath>
 
 #include "common.cuh"
@@ -20,14 +21,26 @@ __device__ LogTab g_logtab;
 
 constexpr int kUThreads = 256;
 constexpr int kUWarps = kUThreads / kWarp;
-static_assert(kUWarps * kSeg == kUTile, "uniform tile");
+constexpr int kUItems = 1;  // one draw per thread (short dependent chains)
+static_assert(kUThreads * kUItems == kUTile, "uniform tile");
 constexpr int kZFrac = 88;  // spacing grid 2^-88
+
+// 1/Z_{N+1} as an xf, once per call by the thread that produced Z_{N+1}
+// (binary64-pair division, out of line; this kernel runs beside the weights
+// pass, so the cost is off the critical path).
+__device__ __noinline__ void store_recip(unsigned long long* dst, u128 t) {
+  const xf r = xf_div(xf_from_u64(1, 0), xf_make(t.hi, t.lo, 0));
+  dst[0] = r.lo;
+  dst[1] = r.hi;
+  dst[2] = (unsigned long long)r.e;
+}
 
 template <bool F32>
 __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, unsigned long long seed,
                                                            unsigned long long inst, u128* __restrict__ Z,
-                                                           u128* __restrict__ Ztot, TileDesc<u128>* desc,
-                                                           unsigned* ctr, int* status, int spin_limit) {
+                                                           u128* __restrict__ Ztot, PathConsts* consts,
+                                                           TileDesc<u128>* desc, unsigned* ctr, int* status,
+                                                           int spin_limit) {
   __shared__ LogTab tab;
   __shared__ u128 s_wsum[kUWarps];
   __shared__ u128 s_woff[kUWarps];
@@ -42,31 +55,32 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
   __syncthreads();
   const long long tile = s_tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long k0 = tile * kUTile + (long long)warp * kSeg + (long long)lane * kSegV;
+  const long long k0 = tile * kUTile + (long long)threadIdx.x * kUItems;
 
-  u128 pre[kSegV];  // lane-local inclusive prefixes
+  u128 pre[kUItems];  // thread-local inclusive prefixes
   u128 run = {0ULL, 0ULL};
+  uint64_t words[4];
+  // each thread evaluates the Philox block of its own draw (four neighbouring
+  // threads share a block; recomputing it is cheaper than the shuffles' wait)
+  philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
+  const unsigned wq = (unsigned)(k0 & 3);
+  const uint64_t word = wq == 0 ? words[0] : wq == 1 ? words[1] : wq == 2 ? words[2] : words[3];
 #pragma unroll
-  for (int j = 0; j < kSegV / 4; ++j) {
-    uint64_t words[4];
-    philox4x64_10((uint64_t)(k0 / 4 + j), 0ULL, 0ULL, 0ULL, seed, inst, words);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const long long k = k0 + j * 4 + q;
-      u128 f = {0ULL, 0ULL};
-      if (k < ndraw) {
-        if (F32) {
-          const float v = (float)(2u * (uint32_t)(words[q] >> 41) + 1u) * 0x1p-24f;  // exact
-          f = f_to_fixed128<kZFrac>(-logf(v));
-        } else {
-          const df z = neg_log_draw(2ULL * (words[q] >> 12) + 1ULL, 53, tab);
-          f = f_to_fixed128<kZFrac>(z.hi);
-          f = (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
-        }
+  for (int q = 0; q < kUItems; ++q) {
+    const long long k = k0 + q;
+    u128 f = {0ULL, 0ULL};
+    if (k < ndraw) {
+      if (F32) {
+        const float v = __int2float_rn((int)(2u * (uint32_t)(word >> 41) + 1u)) * 0x1p-24f;  // exact
+        f = f_to_fixed128<kZFrac>(-logf(v));
+      } else {
+        const df z = neg_log_draw(2ULL * (word >> 12) + 1ULL, 53, tab);
+        f = f_to_fixed128<kZFrac>(z.hi);
+        f = (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
       }
-      run = u128_add(run, f);
-      pre[j * 4 + q] = run;
     }
+    run = u128_add(run, f);
+    pre[q] = run;
   }
   const u128 incl = warp_incl_scan_v(run, lane);
   const u128 lane_off = u128_sub(incl, run);
@@ -89,36 +103,27 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
   __syncthreads();
   const u128 off = u128_add(s_woff[warp], lane_off);
 #pragma unroll
-  for (int i = 0; i < kSegV; ++i) {
-    const long long k = k0 + i;
-    if (k < ndraw - 1) Z[k] = u128_add(off, pre[i]);
-    else if (k == ndraw - 1) *Ztot = u128_add(off, pre[i]);
+  for (int q = 0; q < kUItems; ++q) {
+    const long long k = k0 + q;
+    if (k < ndraw - 1) {
+      Z[k] = u128_add(off, pre[q]);
+    } else if (k == ndraw - 1) {
+      const u128 t = u128_add(off, pre[q]);
+      *Ztot = t;
+      store_recip(consts->invZ, t);
+    }
   }
 }
 
-template <bool F32>
+// U_i = Z_i / Z_{N+1} rounded to binary64: integer multiply by the reciprocal
+// the scan stored, then integer rounding per element, which keeps U monotone
+// in Z.  U <= 1 is enforced (rounding of the reciprocal).
 __global__ void __launch_bounds__(256) k_uniform_norm(long long N, const u128* __restrict__ Z,
-                                                      const u128* __restrict__ Ztot, double* __restrict__ U) {
-  __shared__ double s_r64;
-  __shared__ float s_r32;
-  if (threadIdx.x == 0) {
-    const u128 t = *Ztot;
-    if (F32) s_r32 = __frcp_rn(__uint_as_float(u128_to_f32_bits(t)));
-    else s_r64 = __drcp_rn(__longlong_as_double((long long)u128_to_f64_bits(t)));
-  }
-  __syncthreads();
+                                                      const PathConsts* __restrict__ consts, double* __restrict__ U) {
+  const xf r = {__ldcg(consts->invZ), __ldcg(consts->invZ + 1), (long long)__ldcg(consts->invZ + 2)};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const u128 z = Z[i];
-    long long ub;
-    if (F32) {
-      const float u = __fmul_rn(__uint_as_float(u128_to_f32_bits(z)), s_r32);
-      ub = (long long)f32_to_f64_bits(__float_as_uint(u));
-    } else {
-      const double u = __dmul_rn(__longlong_as_double((long long)u128_to_f64_bits(z)), s_r64);
-      ub = __double_as_longlong(u);
-    }
-    // U <= 1 (the product of rounded values may exceed 1 by an ulp)
+    long long ub = (long long)xf_to_f64_bits(xf_mul_u128(r, Z[i]));
     if (ub > 0x3FF0000000000000LL) ub = 0x3FF0000000000000LL;
     U[i] = __longlong_as_double(ub);
   }
@@ -131,7 +136,8 @@ __global__ void k_philox_words(unsigned long long seed, unsigned long long inst,
     const unsigned long long k = first + (unsigned long long)i;
     uint64_t w[4];
     philox4x64_10(k / 4, 0ULL, 0ULL, 0ULL, seed, inst, w);
-    out[i] = w[k % 4];
+    const unsigned q = (unsigned)(k & 3);
+    out[i] = q == 0 ? w[0] : q == 1 ? w[1] : q == 2 ? w[2] : w[3];
   }
 }
 
@@ -149,25 +155,25 @@ cudaError_t init_log_table() {
 }
 
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,
-                                void* Ztot, void* desc, unsigned* ctr, int* status, int spin_limit, cudaStream_t st) {
+                                void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
+                                int spin_limit, cudaStream_t st) {
   const long long tiles = (ndraw + kUTile - 1) / kUTile;
   if (tiles <= 0) return cudaSuccess;
   if (f32)
-    k_uniform_scan<true><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot,
+    k_uniform_scan<true><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
                                                                 (TileDesc<u128>*)desc, ctr, status, spin_limit);
   else
-    k_uniform_scan<false><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot,
+    k_uniform_scan<false><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
                                                                  (TileDesc<u128>*)desc, ctr, status, spin_limit);
   return cudaGetLastError();
 }
 
-cudaError_t launch_uniform_norm(bool f32, long long N, const void* Z, const void* Ztot, double* U, cudaStream_t st) {
+cudaError_t launch_uniform_norm(long long N, const void* Z, const PathConsts* consts, double* U, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   long long blocks = (N + 255) / 256;
   const long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
-  if (f32) k_uniform_norm<true><<<(unsigned)blocks, 256, 0, st>>>(N, (const u128*)Z, (const u128*)Ztot, U);
-  else k_uniform_norm<false><<<(unsigned)blocks, 256, 0, st>>>(N, (const u128*)Z, (const u128*)Ztot, U);
+  k_uniform_norm<<<(unsigned)blocks, 256, 0, st>>>(N, (const u128*)Z, consts, U);
   return cudaGetLastError();
 }
 

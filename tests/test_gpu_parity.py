@@ -261,8 +261,9 @@ def test_zero_sum_latches_status(g, h):
 
 def test_bounded_wait_times_out_and_context_survives(g, h):
     """Fault injection on the host side: the first look-back tile withholds
-    its publication; every later tile's wait runs out after spin_limit polls."""
-    M = 64 * 4096
+    its publication; every later tile's wait runs out after spin_limit polls.
+    (The segment-prefix scan chains tiles of 2048 segments of 512 weights.)"""
+    M = 3 * 2048 * 512 + 1000
     w = workloads.weights_small(M, seed=2)
     W = torch.empty(M, dtype=torch.float64, device="cuda")
     g.rs_cumulative(h.h, dev(w), M, W, g.opts(spin_limit=200, debug_flags=1))
