@@ -81,10 +81,11 @@ typedef struct {
   int32_t leaf_L;      /* DaC: samples per leaf (power of two 1..1024; 0 = choose from M/N) */
   int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 4096) */
   int32_t spin_limit;  /* bounded-wait iterations before RS_ETIMEOUT (0 = default) */
-  int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of the
-                          weights pass withholds its look-back publication, so every
-                          later tile's bounded wait runs out and RS_ETIMEOUT is
-                          latched (results are then unspecified).  Nothing faults. */
+  int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of every
+                          look-back scan of the call (spacings, tile prefixes)
+                          withholds its publication, so every later tile's bounded
+                          wait runs out and RS_ETIMEOUT is latched (results are then
+                          unspecified).  Nothing faults. */
   int32_t reserved[2]; /* must be zero */
 } rs_opts;
 

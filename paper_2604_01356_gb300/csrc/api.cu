@@ -164,17 +164,17 @@ rs_status ensure_ws(rs_handle* h, size_t bytes) {
 // that a single memset clears them.
 struct Plan {
   // weights side
-  long long M = 0, nseg = 0, wtiles = 0;
+  long long M = 0, nseg = 0, ntile = 0, pblocks = 0;
   int nlev = 0;
   long long lvl_n[kMaxLevels] = {0};
-  size_t o_wdesc = 0, o_seg = 0, o_tagg = 0, o_lvl[kMaxLevels] = {0}, o_consts = 0;
+  size_t o_wdesc = 0, o_seg = 0, o_emax = 0, o_pre = 0, o_xin = 0, o_xagg = 0, o_lvl[kMaxLevels] = {0}, o_consts = 0;
   // uniforms side
   long long N = 0, ndraw = 0, utiles = 0;
   size_t o_udesc = 0, o_Z = 0, o_Ztot = 0, o_U = 0;
   size_t o_ctr = 0, clear_bytes = 0, bytes = 0;
 };
 
-Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) {
+Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U, bool need_W = false) {
   Plan p;
   Layout L;
   p.o_ctr = L.take(256);  // [0]: uniform tile counter, [1]: weight tile counter
@@ -187,13 +187,20 @@ Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) 
   if (need_w) {
     p.M = M;
     p.nseg = (M + kSegLen - 1) / kSegLen;
-    p.wtiles = (p.nseg + kSegPrefixTile - 1) / kSegPrefixTile;
-    p.o_wdesc = L.take((size_t)p.wtiles * kTileDescBytes);
+    p.ntile = (p.nseg + kSegsPerTile - 1) / kSegsPerTile;
+    p.pblocks = (p.ntile + kPrefixTilesPerBlock - 1) / kPrefixTilesPerBlock;
+    p.o_wdesc = L.take((size_t)p.pblocks * kTileDescBytes);
   }
   p.clear_bytes = L.off;
   if (need_w) {
     p.o_seg = L.take((size_t)p.nseg * sizeof(SegRec));
-    p.o_tagg = L.take((size_t)((p.nseg + 7) / 8) * kTileAggBytes);
+    // per-reduce-block exponent maxima, padded to whole 16-byte groups
+    p.o_emax = L.take((size_t)((p.ntile + 3) / 4) * 16);
+    p.o_pre = L.take((size_t)p.nseg * sizeof(SegPre));
+    if (need_W) {
+      p.o_xin = L.take((size_t)p.nseg * sizeof(SegX));
+      p.o_xagg = L.take((size_t)p.pblocks * sizeof(SegX));
+    }
     long long n = p.nseg;
     p.nlev = 0;
     while (true) {
@@ -217,7 +224,7 @@ Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U) 
 SegIndex index_of(rs_handle* h, const Plan& p) {
   SegIndex idx;
   memset(&idx, 0, sizeof(idx));
-  idx.nseg = p.nseg;
+  idx.n = p.nseg;
   idx.nlev = p.nlev;
   for (int l = 0; l < p.nlev; ++l) {
     idx.lvl_n[l] = p.lvl_n[l];
@@ -277,7 +284,7 @@ rs_status enqueue_uniforms(rs_handle* h, const Plan& p, bool f32, uint64_t seed,
     RS_TRACE(h, "uniform_scan", st);
     RS_CK(h, launch_uniform_scan(f32, p.ndraw, seed, inst, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot),
                                  at<PathConsts>(h, p.o_consts), at<void>(h, p.o_udesc), ctr_u(h, p), h->status,
-                                 o.spin, st));
+                                 o.spin, o.debug & 1, st));
   }
   if (U_out) {
     RS_TRACE(h, "uniform_norm", st);
@@ -298,9 +305,10 @@ rs_status enqueue_prefix(rs_handle* h, const Plan& p, const Opts& o, bool f32, b
                          cudaStream_t st) {
   RS_TRACE(h, "seg_prefix", st);
   const SegIndex idx = index_of(h, p);
-  RS_CK(h, launch_seg_prefix(f32, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), idx, at<void>(h, p.o_wdesc),
-                             ctr_w(h, p), at<PathConsts>(h, p.o_consts), with_z, need_invS, h->status, o.spin,
-                             o.debug & 1, st));
+  RS_CK(h, launch_seg_prefix(f32, p.M, at<SegRec>(h, p.o_seg), at<int>(h, p.o_emax), at<SegPre>(h, p.o_pre),
+                             p.o_xin ? at<SegX>(h, p.o_xin) : nullptr, p.o_xagg ? at<SegX>(h, p.o_xagg) : nullptr, idx,
+                             at<void>(h, p.o_wdesc), ctr_w(h, p), at<PathConsts>(h, p.o_consts), with_z, need_invS,
+                             h->status, o.spin, o.debug & 1, st));
   return RS_OK;
 }
 
@@ -309,7 +317,7 @@ rs_status enqueue_pass1(rs_handle* h, const Plan& p, const Opts& o, bool f32, bo
                         bool with_z, bool need_invS, cudaStream_t st) {
   {
     RS_TRACE(h, "w_reduce", st);
-    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), h->status, st));
+    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<int>(h, p.o_emax), h->status, st));
   }
   return enqueue_prefix(h, p, o, f32, with_z, need_invS, st);
 }
@@ -317,7 +325,8 @@ rs_status enqueue_pass1(rs_handle* h, const Plan& p, const Opts& o, bool f32, bo
 rs_status enqueue_write(rs_handle* h, const Plan& p, bool f32, bool vec, const void* w, double* W_out,
                         cudaStream_t st) {
   RS_TRACE(h, "w_write", st);
-  RS_CK(h, launch_w_write(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<PathConsts>(h, p.o_consts), W_out, st));
+  RS_CK(h, launch_w_write(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<SegPre>(h, p.o_pre), at<SegX>(h, p.o_xin),
+                          at<SegX>(h, p.o_xagg), at<PathConsts>(h, p.o_consts), W_out, st));
   return RS_OK;
 }
 
@@ -502,7 +511,7 @@ rs_status rs_cumulative(rs_handle* h, const void* w, int64_t M, double* W_out, c
   if (!w || !aligned(w, f32 ? 4 : 8)) return fail(h, RS_EINVAL, "w must be a non-NULL aligned device pointer");
   if (!W_out || !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be a non-NULL 8-byte aligned pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Plan p = make_plan(M, 0, true, false, false);
+  const Plan p = make_plan(M, 0, true, false, false, true);
   if ((s = ensure_ws(h, p.bytes))) return s;
   const bool vec = aligned(w, 16);
   if ((s = enqueue_clear(h, p, st))) return s;
@@ -523,7 +532,7 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   if (W_out && !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be 8-byte aligned");
   if (N == 0 && !W_out) return RS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const Plan p = make_plan(M, N, true, N > 0, false);
+  const Plan p = make_plan(M, N, true, N > 0, false, W_out != nullptr);
   if ((s = ensure_ws(h, p.bytes))) return s;
   const bool vec = aligned(w, 16);
   // fork: the workspace clear and the spacing scan (independent of w) run on
@@ -538,15 +547,15 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   RS_CK(h, cudaEventRecord(h->ev_join, h->side));
   {
     RS_TRACE(h, "w_reduce", st);
-    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<void>(h, p.o_tagg), h->status, st));
+    RS_CK(h, launch_w_reduce(f32, vec, w, p.M, at<SegRec>(h, p.o_seg), at<int>(h, p.o_emax), h->status, st));
   }
   RS_CK(h, cudaStreamWaitEvent(st, h->ev_join, 0));
   if ((s = enqueue_prefix(h, p, o, f32, N > 0, W_out != nullptr, st))) return s;
   if (N > 0) {
     RS_TRACE(h, "map_seg", st);
     const SegIndex idx = index_of(h, p);
-    RS_CK(h, launch_map_seg(f32, vec, w, M, at<SegRec>(h, p.o_seg), idx, at<PathConsts>(h, p.o_consts),
-                            at<void>(h, p.o_Z), N, group_size(N), out_idx, st));
+    RS_CK(h, launch_map_seg(f32, vec, w, M, at<SegRec>(h, p.o_seg), at<SegPre>(h, p.o_pre), idx,
+                            at<PathConsts>(h, p.o_consts), at<void>(h, p.o_Z), N, group_size(N), out_idx, st));
   }
   if (W_out) return enqueue_write(h, p, f32, vec, w, W_out, st);
   return RS_OK;

@@ -240,6 +240,22 @@ __device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {
 }
 __device__ __forceinline__ bool u128_is_zero(u128 a) { return (a.lo | a.hi) == 0; }
 
+// Monotone 64-bit search key of a 128-bit unsigned integer: position of the
+// leading bit (7 bits) then the next 57 bits.  Keeps relative precision for
+// small values, unlike the high word alone.
+__device__ __forceinline__ unsigned long long u128_key(u128 a) {
+  if (u128_is_zero(a)) return 0ULL;
+  const int lz = a.hi ? __clzll(a.hi) : 64 + __clzll(a.lo);
+  uint64_t h = a.hi, l = a.lo;
+  if (lz < 64) {
+    if (lz) h = (h << lz) | (l >> (64 - lz));
+  } else {
+    h = l << (lz - 64);
+  }
+  // h has its leading bit at 63: drop it, keep 57 bits below it
+  return ((unsigned long long)(128 - lz) << 57) | ((h << 1) >> 7);
+}
+
 // Bit pattern of the binary64 nearest to a 128-bit unsigned integer (round
 // half to even), integer operations only.
 __device__ __forceinline__ uint64_t u128_to_f64_bits(u128 a) {

@@ -16,51 +16,56 @@ struct SegRec {
 };
 static_assert(sizeof(SegRec) == 16, "SegRec layout");
 
-// One record per tile of 8 segments (4096 weights), written by the tile
-// prefix scan: P = sum of all earlier tiles as Pm * 2^Pe (128-bit mantissa),
-// key = P truncated to binary64 (bit pattern), the search key.
-constexpr int kSegsPerTile = 8;
-struct TileRec {
-  unsigned long long Pm_lo, Pm_hi;
-  long long Pe;
-  unsigned long long key;
-};
-static_assert(sizeof(TileRec) == 32, "TileRec layout");
+// After the reduce pass every segment sum is put on one global fixed-point
+// grid: unit 2^ge with ge = Emax - bias - shift - kGridHead, Emax the largest
+// segment exponent.  A segment's sum becomes F * 2^(E - Emax + kGridHead) in
+// grid units (truncated below one unit), every prefix is an exact unsigned
+// 128-bit integer (the sum of up to 2^22 segments stays below 2^126), and the
+// truncation costs at most nseg units = 2^-71 of the total.
+constexpr int kGridHead = 41;
+constexpr int kSegsPerTile = 8;  // segments per reduce block, per prefix-scan thread
 
-// Search index over tile prefixes: level 0 holds the key of every tile, level
-// l every 32^l-th one (non-negative binary64 values order like their
-// unsigned bit patterns).  The top level has <= 32 entries.
+// Exclusive prefix of one segment on the global grid.
+struct SegPre {
+  unsigned long long lo, hi;
+};
+static_assert(sizeof(SegPre) == 16, "SegPre layout");
+
+// Prefix of a segment as an xf value (128-bit mantissa, exponent), used only
+// when W itself is written, for the leading segments whose prefix is too small
+// for the global grid's absolute resolution: the exclusive prefix inside its
+// block of the prefix scan (xin) and every block's total (xagg).
+struct SegX {
+  unsigned long long lo, hi;
+  long long e, pad;
+};
+static_assert(sizeof(SegX) == 32, "SegX layout");
+
+// Search index over segment prefixes: level 0 holds the high 64 bits of every
+// segment's prefix, level l every 32^l-th one.  The top level has <= 32
+// entries.
 constexpr int kMaxLevels = 8;
 struct SegIndex {
-  long long n;  // tiles
+  long long n;  // segments
   int nlev;
   long long lvl_n[kMaxLevels];
   unsigned long long* lvl[kMaxLevels];
 };
 
-// Per-call constants (24-byte xf values: mantissa lo, hi, exponent):
-// invZ = 1/Z_{N+1} (written by the spacing scan), S = total weight, invS = 1/S
-// (only when W itself is written) and c = S / Z_{N+1} (written by the
-// segment-prefix scan).
+// Per-call constants.  S: the total on the global grid (u128) and the grid
+// exponent ge; xf values (mantissa lo, hi, exponent): invZ = 1/Z_{N+1}
+// (written by the spacing scan), c = S_grid / Z_{N+1} (grid units per spacing
+// unit), invS = 1/S_grid (only when W itself is written).
 struct PathConsts {
-  unsigned long long S[3];
+  unsigned long long S[2];
+  long long ge;
+  long long Emax;
   unsigned long long invS[3];
   unsigned long long c[3];
   unsigned long long invZ[3];
-  unsigned long long pad[4];
+  unsigned long long pad[3];
 };
 static_assert(sizeof(PathConsts) == 128, "PathConsts layout");
-
-// Search index over segment prefixes: level 0 holds the bit pattern of P_hi
-// of every segment, level l every 32^l-th one (non-negative binary64 values
-// order like their unsigned bit patterns).  The top level has <= 32 entries.
-constexpr int kMaxLevels = 8;
-struct SegIndex {
-  long long nseg;
-  int nlev;
-  long long lvl_n[kMaxLevels];
-  unsigned long long* lvl[kMaxLevels];
-};
 
 // Weights per segment (one warp, 16 per lane) and look-back descriptor size.
 constexpr int kSegLen = 512;
@@ -75,25 +80,25 @@ cudaError_t init_log_table();
 struct PathConsts;
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst,
                                 void* Z, void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
-                                int spin_limit, cudaStream_t st);
+                                int spin_limit, bool withhold_first, cudaStream_t st);
 cudaError_t launch_uniform_norm(long long N, const void* Z, const PathConsts* consts, double* U, cudaStream_t st);
 cudaError_t launch_philox(unsigned long long seed, unsigned long long inst, unsigned long long first, long long n,
                           unsigned long long* out, cudaStream_t st);
 
 // --- weights (Eq. 3) ------------------------------------------------------
-// Tile aggregates of the reduce pass: one 24-byte value per 8 segments.
-constexpr int kTileAggBytes = 24;
-constexpr int kTilePrefixPerBlock = 4096;  // tiles per block of the tile-prefix scan
-cudaError_t launch_w_reduce(bool f32, bool vec, const void* w, long long M, SegRec* seg, void* tagg, int* status,
+constexpr int kPrefixTilesPerBlock = 256;  // threads (one tile of 8 segments each) per prefix block
+cudaError_t launch_w_reduce(bool f32, bool vec, const void* w, long long M, SegRec* seg, int* emax_blk, int* status,
                             cudaStream_t st);
-cudaError_t launch_tile_prefix(bool f32, long long M, const void* tagg, TileRec* tiles, const SegIndex& idx,
-                               void* desc, unsigned* ctr, PathConsts* consts, bool with_z, bool need_invS,
-                               int* status, int spin_limit, bool withhold_first, cudaStream_t st);
-cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const TileRec* tiles,
-                           const PathConsts* consts, double* W, cudaStream_t st);
+// xin/xagg (nullptr when W is not written) receive the xf prefixes.
+cudaError_t launch_seg_prefix(bool f32, long long M, const SegRec* seg, const int* emax_blk, SegPre* pre,
+                              SegX* xin, SegX* xagg, const SegIndex& idx, void* desc, unsigned* ctr,
+                              PathConsts* consts, bool with_z, bool need_invS, int* status, int spin_limit,
+                              bool withhold_first, cudaStream_t st);
+cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
+                           const SegX* xin, const SegX* xagg, const PathConsts* consts, double* W, cudaStream_t st);
 
 // --- maps (Eq. 2; Algorithms 3, 4, 5) -------------------------------------
-cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const TileRec* tiles,
+cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
                            const SegIndex& idx, const PathConsts* consts, const void* Z, long long N, int G, int* out,
                            cudaStream_t st);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);

@@ -5,10 +5,11 @@
 //               conquer of Algorithm 5 applied first to the segment level of
 //               W: U is split into groups of G consecutive samples (one warp
 //               each); the group's first sample locates its segment with a
-//               32-ary search down the segment index; later samples of the
-//               group walk forward (Algorithm 4's merge walk, with a 32-wide
-//               skip); inside a segment the answer comes from exact integer
-//               prefixes of the re-read weights.
+//               search down the segment index (integer prefixes on the global
+//               grid); later samples of the group walk forward (Algorithm 4's
+//               merge walk, with a 32-segment skip); inside a segment the
+//               answer comes from exact integer prefixes of the re-read
+//               weights.
 // k_map_dac     Algorithm 5 on a given W: split U every L samples, find the
 //               split points by warp-cooperative 32-ary search, then resolve
 //               each leaf inside the W range its two split points bound -
@@ -66,42 +67,39 @@ __device__ __forceinline__ void load_blocked(const T* __restrict__ w, long long 
   }
 }
 
-__device__ __forceinline__ xf rec_P(const SegRec* __restrict__ seg, long long s) {
-  return {__ldcg(&seg[s].Pm_lo), __ldcg(&seg[s].Pm_hi), (long long)__ldcg((const unsigned long long*)&seg[s].Pe)};
+__device__ __forceinline__ u128 seg_pre(const SegPre* __restrict__ pre, long long s) {
+  return u128{__ldcg(&pre[s].lo), __ldcg(&pre[s].hi)};
+}
+__device__ __forceinline__ bool u128_lt(const u128& a, const u128& b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 __device__ __forceinline__ xf ld_consts_xf(const unsigned long long* p) {
   return {__ldcg(p), __ldcg(p + 1), (long long)__ldcg(p + 2)};
 }
 
 // Last segment s with P_s < key: a 32-ary search down the index on the
-// binary64 keys (rounding is monotone, so it can only stop early on ties),
-// then an exact forward / backward fix-up on the 128-bit values.
-__device__ __forceinline__ long long fixup_segment(const SegRec* __restrict__ seg, long long nseg, long long s,
-                                                   const xf& key) {
+// monotone 64-bit keys, then an exact fix-up on the 128-bit prefixes only
+// when the keys do not already separate key from its neighbours.
+__device__ __forceinline__ long long fixup_seg(const SegPre* __restrict__ pre, long long n, long long s,
+                                               const u128& key) {
   int guard = 0;
-  while (s + 1 < nseg && xf_lt(rec_P(seg, s + 1), key) && ++guard < 4096) ++s;
-  while (s > 0 && xf_le(key, rec_P(seg, s)) && ++guard < 8192) --s;
+  while (s + 1 < n && u128_lt(seg_pre(pre, s + 1), key) && ++guard < 4096) ++s;
+  while (s > 0 && !u128_lt(seg_pre(pre, s), key) && ++guard < 8192) --s;
   return s;
 }
-// Level-0 step shared by both searches: within the 32 segments of node c,
-// the last one whose key is below kb; exact fix-up only on ties or at the
-// window's edge (key(P_s) < kb < key(P_{s+1}) strictly proves
-// P_s < key <= P_{s+1}, since truncation to binary64 is monotone).
-__device__ __forceinline__ long long level0_step(const SegRec* __restrict__ seg, const SegIndex& idx, long long c,
-                                                 unsigned long long kb, const xf& key, int lane) {
+__device__ __forceinline__ long long level0_step(const SegPre* __restrict__ pre, const SegIndex& idx, long long c,
+                                                 unsigned long long kb, const u128& key, int lane) {
   const long long j = c * 32 + lane;
   const unsigned long long e = j < idx.lvl_n[0] ? __ldcg(idx.lvl[0] + j) : ~0ULL;
   const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
   const long long s = c * 32 + (cnt > 0 ? cnt - 1 : 0);
   const unsigned long long next = __shfl_sync(0xFFFFFFFFu, e, cnt & 31);
+  // key(P_s) < kb < key(P_{s+1}) proves P_s < key <= P_{s+1} (monotone keys)
   if (cnt > 0 && cnt < 32 && next != kb) return s;
-  return fixup_segment(seg, idx.nseg, s, key);
+  return fixup_seg(pre, idx.n, s, key);
 }
-
-// Last segment s with P_s < key: 32-ary descent of the index in global
-// memory (general case).
-__device__ __forceinline__ long long locate_segment(const SegRec* __restrict__ seg, const SegIndex& idx,
-                                                    unsigned long long kb, const xf& key, int lane) {
+__device__ __forceinline__ long long locate_seg(const SegPre* __restrict__ pre, const SegIndex& idx,
+                                                unsigned long long kb, const u128& key, int lane) {
   long long c = 0;
   for (int l = idx.nlev - 1; l >= 1; --l) {
     const long long j = c * 32 + lane;
@@ -109,33 +107,30 @@ __device__ __forceinline__ long long locate_segment(const SegRec* __restrict__ s
     const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
     c = c * 32 + (cnt > 0 ? cnt - 1 : 0);
   }
-  return level0_step(seg, idx, c, kb, key, lane);
+  return level0_step(pre, idx, c, kb, key, lane);
 }
-
-// Same with level 1 of the index staged in shared memory (binary search there,
-// then one global level-0 window).
-__device__ __forceinline__ long long locate_segment_smem(const SegRec* __restrict__ seg, const SegIndex& idx,
-                                                         const unsigned long long* __restrict__ top, int ntop,
-                                                         unsigned long long kb, const xf& key, int lane) {
+// Same with level 1 of the index staged in shared memory.
+__device__ __forceinline__ long long locate_seg_smem(const SegPre* __restrict__ pre, const SegIndex& idx,
+                                                     const unsigned long long* __restrict__ top, int ntop,
+                                                     unsigned long long kb, const u128& key, int lane) {
   int lo = 0, hi = ntop;  // first entry >= kb
   while (lo < hi) {
     const int m = (lo + hi) >> 1;
     if (top[m] < kb) lo = m + 1;
     else hi = m;
   }
-  return level0_step(seg, idx, lo > 0 ? lo - 1 : 0, kb, key, lane);
+  return level0_step(pre, idx, lo > 0 ? lo - 1 : 0, kb, key, lane);
 }
 
 // Head segment of binary64 weights: number of elements j with
-// sum_{k<=j} w_k < rem, rem = key - P_s.  The weights are put on a 128-bit
-// grid scaled to rem (unit 2^(rem.e + 25), so rem is about 2^100 units) and
-// summed with saturation at 2^102: the decision is exact up to 512 units,
-// i.e. 2^-91 of rem, whatever the dynamic range of the segment.
+// sum_{k<=j} w_k < rem (rem = key - P_s as a value).  The weights are put on a
+// 128-bit grid scaled to rem (unit 2^(rem.e + 25), so rem is about 2^100
+// units) and summed with saturation at 2^102: the decision is exact up to 512
+// units, i.e. 2^-91 of rem, whatever the dynamic range of the segment.
 __device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
   const u128 s = u128_add(a, b);
   return (s.hi >> 38) ? u128{0ULL, 1ULL << 38} : s;  // cap at 2^102
 }
-// One binary64 weight in units of 2^ue (saturated at 2^102).
 __device__ __forceinline__ u128 head_val(uint64_t b, long long ue) {
   const uint32_t t = (uint32_t)(b >> 52);
   if (t >= 0x7FFu) return u128{0ULL, 0ULL};
@@ -150,10 +145,9 @@ __device__ __forceinline__ u128 head_val(uint64_t b, long long ue) {
   return sh > -64 ? u128{m >> (-sh), 0ULL} : u128{0ULL, 0ULL};
 }
 template <bool kVec>
-__device__ __forceinline__ int head_count(const double* __restrict__ w, long long base, long long M, const xf& Ps,
-                                          const xf& key, int lane) {
+__device__ __forceinline__ int head_count(const double* __restrict__ w, long long base, long long M, const xf& rem,
+                                          int lane) {
   using Tr = FixedTraits<double>;
-  const xf rem = xf_sub(key, Ps);
   if (xf_zero(rem)) return 0;
   // R = rem / unit = rem.m >> 25, in [2^100, 2^101)
   uint64_t rh = rem.hi, rl = rem.lo;
@@ -164,7 +158,6 @@ __device__ __forceinline__ int head_count(const double* __restrict__ w, long lon
   u128 run = {0ULL, 0ULL};
 #pragma unroll
   for (int i = 0; i < kSegV; ++i) run = sat_add(run, head_val(b[i], ue));
-  // exclusive offset of this lane (saturating warp scan)
   u128 incl = run;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -184,34 +177,35 @@ __device__ __forceinline__ int head_count(const double* __restrict__ w, long lon
   return cnt;
 }
 template <bool kVec>
-__device__ __forceinline__ int head_count(const float*, long long, long long, const xf&, const xf&, int) {
+__device__ __forceinline__ int head_count(const float*, long long, long long, const xf&, int) {
   return 0;  // binary32 weights never need it: their grid is finer than the tolerance
 }
 
-// K = ceil(rem / 2^ue) clamped to [1, F] (rem is a normalised xf).
-__device__ __forceinline__ unsigned long long ceil_units(const xf& rem, long long ue, unsigned long long F) {
-  if (xf_zero(rem)) return 1;
-  const long long sh = rem.e - ue;
+// K = ceil(rem / 2^sh) clamped to [1, F]: the segment-grid target of a key
+// that lies rem grid units above the segment's start.
+__device__ __forceinline__ unsigned long long ceil_units(u128 rem, int sh, unsigned long long F) {
+  if (u128_is_zero(rem)) return 1;
   unsigned long long K;
   if (sh >= 0) {
-    K = F;  // rem >= 2^125 units
-  } else if (sh <= -128) {
-    K = 1;
-  } else {
-    const int r = (int)(-sh);
-    uint64_t hi = rem.hi, lo = rem.lo;
-    // add 2^r - 1, then shift right by r
-    uint64_t ah = 0, al = 0;
-    if (r >= 64) {
-      ah = (r == 64) ? 0 : ((1ULL << (r - 64)) - 1);
-      al = ~0ULL;
+    if (sh >= 128) {
+      K = 1;
     } else {
-      al = (1ULL << r) - 1;
+      uint64_t ah = 0, al = 0;  // 2^sh - 1
+      if (sh >= 64) {
+        ah = (sh == 64) ? 0 : ((1ULL << (sh - 64)) - 1);
+        al = ~0ULL;
+      } else {
+        al = (1ULL << sh) - 1;
+      }
+      uint64_t nl = rem.lo + al;
+      uint64_t nh = rem.hi + ah + (nl < rem.lo ? 1ULL : 0ULL);
+      shr128(nh, nl, sh);
+      K = nh ? F : nl;
     }
-    uint64_t nl = lo + al;
-    uint64_t nh = hi + ah + (nl < lo ? 1ULL : 0ULL);
-    shr128(nh, nl, r);
-    K = nh ? F : nl;
+  } else {
+    // rem * 2^-sh; anything at or above 2^63 is past F anyway
+    const int ls = -sh;
+    K = (rem.hi || ls >= 63 || (rem.lo >> (63 - ls))) ? F : (rem.lo << ls);
   }
   if (K > F) K = F;
   if (K < 1) K = 1;
@@ -220,15 +214,17 @@ __device__ __forceinline__ unsigned long long ceil_units(const xf& rem, long lon
 
 template <typename T, bool kVec>
 __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, long long M,
-                                                    const SegRec* __restrict__ seg, SegIndex idx,
-                                                    const PathConsts* __restrict__ consts,
+                                                    const SegRec* __restrict__ seg, const SegPre* __restrict__ pre,
+                                                    SegIndex idx, const PathConsts* __restrict__ consts,
                                                     const u128* __restrict__ Z, long long N, int G, int ntop,
                                                     int* __restrict__ out) {
   using Tr = FixedTraits<T>;
   using Bits = typename Tr::Bits;
-  constexpr int kBS = Tr::kBias + Tr::kShift;
   extern __shared__ unsigned long long s_top[];  // level 1 of the index when ntop > 0
-  __shared__ xf s_c, s_S;
+  __shared__ xf s_c;
+  __shared__ u128 s_S;
+  __shared__ long long s_ge;
+  __shared__ int s_Emax;
   const long long gw0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   // the first sample's spacing sum is fetched while the index is staged
   u128 z_first = {0ULL, 0ULL};
@@ -236,19 +232,21 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
   for (int t = threadIdx.x; t < ntop; t += blockDim.x) s_top[t] = __ldcg(idx.lvl[1] + t);
   if (threadIdx.x == 0) {
     s_c = ld_consts_xf(consts->c);
-    s_S = ld_consts_xf(consts->S);
+    s_S = u128{__ldcg(consts->S), __ldcg(consts->S + 1)};
+    s_ge = (long long)__ldcg((const unsigned long long*)&consts->ge);
+    s_Emax = (int)__ldcg((const unsigned long long*)&consts->Emax);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long gw = gw0;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nseg = idx.nseg;
+  const long long nseg = idx.n;
   for (long long g = gw; g * (long long)G < N; g += nw) {
     const long long i0 = g * (long long)G;
     const long long i1 = (i0 + G < N) ? i0 + G : N;
     long long s = -1;  // segment held in registers
-    xf Ps = lb_zero<xf>(), Pn = lb_zero<xf>();
-    int E = 1, len = 0;
+    u128 Ps = {0ULL, 0ULL}, Pn = {0ULL, 0ULL};
+    int sh = 0, len = 0;
     bool head = false;
     unsigned long long F = 0;
     uint64_t pref[kSegV];
@@ -256,37 +254,55 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
     for (int q = 0; q < kSegV; ++q) pref[q] = 0;
     for (long long i = i0; i < i1; ++i) {
       const u128 z = (g == gw0 && i == i0) ? z_first : Z[i];
-      // key = U_i * S = Z_i * (S / Z_{N+1}): exact integer product
-      const xf key = xf_mul_u128(s_c, z);
-      if (s < 0 || !(xf_lt(Ps, key) && xf_le(key, Pn))) {
-        const unsigned long long kb = xf_key(key);
+      // key = U_i * S in grid units, rounded up: ceil(Z_i * (S / Z_{N+1}))
+      const xf kx = xf_mul_u128(s_c, z);
+      u128 key = {0ULL, 0ULL};
+      if (!xf_zero(kx)) {
+        uint64_t kh = kx.hi, kl = kx.lo;
+        if (kx.e >= 0) {
+          shl128(kh, kl, kx.e > 1 ? 1 : (int)kx.e);  // key <= S < 2^126: e <= 1
+        } else {
+          const int r = kx.e < -127 ? 128 : (int)(-kx.e);
+          uint64_t th = kh, tl = kl;
+          shr128(th, tl, r);
+          uint64_t bh = th, bl = tl;
+          shl128(bh, bl, r < 128 ? r : 0);
+          const bool frac = r >= 128 ? true : (bh != kh || bl != kl);
+          kh = th;
+          kl = tl + (frac ? 1ULL : 0ULL);
+          if (kl < tl) ++kh;
+        }
+        key = u128{kl, kh};
+      }
+      if (s < 0 || !(u128_lt(Ps, key) && !u128_lt(Pn, key))) {
+        const unsigned long long kb = u128_key(key);
         long long ns = -1;
-        if (s >= 0 && xf_lt(Pn, key)) {
+        if (s >= 0 && u128_lt(Pn, key)) {
           // forward skip over the next 32 segments (merge walk)
           const long long j = s + 1 + lane;
           const unsigned long long e = j < nseg ? __ldcg(idx.lvl[0] + j) : ~0ULL;
           const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
-          if (cnt < 32) ns = fixup_segment(seg, nseg, s + cnt, key);
+          if (cnt < 32) ns = fixup_seg(pre, nseg, s + cnt, key);
         }
         if (ns < 0)
-          ns = ntop > 0 ? locate_segment_smem(seg, idx, s_top, ntop, kb, key, lane)
-                        : locate_segment(seg, idx, kb, key, lane);
+          ns = ntop > 0 ? locate_seg_smem(pre, idx, s_top, ntop, kb, key, lane) : locate_seg(pre, idx, kb, key, lane);
         s = ns;
-        // record, next prefix and the segment's weights are independent loads
+        // the segment's record, prefixes and weights are independent loads
         Bits b[kSegV];
         load_blocked<T, kVec>(w, s * kSeg, M, lane, b);
         const SegRec r = seg[s];
-        Pn = (s + 1 < nseg) ? rec_P(seg, s + 1) : s_S;
-        Ps = xf{r.Pm_lo, r.Pm_hi, r.Pe};
-        E = r.E;
+        Ps = seg_pre(pre, s);
+        Pn = (s + 1 < nseg) ? seg_pre(pre, s + 1) : s_S;
+        sh = r.E - s_Emax + kGridHead;
         len = r.len;
         F = r.F;
-        head = sizeof(T) == 8 && head_segment(Ps, E, kBS);
+        const xf Px = xf_make(Ps.hi, Ps.lo, 0);
+        head = sizeof(T) == 8 && (xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50);
         if (!head) {
           uint64_t run = 0;
 #pragma unroll
           for (int q = 0; q < kSegV; ++q) {
-            run += Tr::fixed(b[q], (uint32_t)E);
+            run += Tr::fixed(b[q], (uint32_t)r.E);
             pref[q] = run;
           }
           const uint64_t off = warp_incl_scan_u64(run, lane) - run;
@@ -294,12 +310,13 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
           for (int q = 0; q < kSegV; ++q) pref[q] += off;
         }
       }
+      const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
       int cnt;
       if (head) {
-        cnt = head_count<kVec>(w, s * kSeg, M, Ps, key, lane);
+        cnt = head_count<kVec>(w, s * kSeg, M, xf_make(rem.hi, rem.lo, s_ge), lane);
       } else {
-        // first element whose exact prefix reaches K = ceil((key - P_s)/unit)
-        const unsigned long long K = ceil_units(xf_sub(key, Ps), (long long)(E - kBS), F);
+        // first element whose exact prefix reaches K = ceil(rem / unit_s)
+        const unsigned long long K = ceil_units(rem, sh, F);
         cnt = 0;
 #pragma unroll
         for (int q = 0; q < kSegV; ++q) cnt += pref[q] < K ? 1 : 0;
@@ -319,7 +336,7 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
 constexpr int kMapTopMax = 6144;  // entries (48 KB, the default dynamic shared-memory limit)
 
 template <typename T, bool kVec>
-static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, const SegIndex& idx,
+static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, const SegPre* pre, const SegIndex& idx,
                              const PathConsts* consts, const void* Z, long long N, int G, int* out, cudaStream_t st) {
   const long long groups = (N + G - 1) / G;
   long long blocks = (groups + 7) / 8;
@@ -330,18 +347,19 @@ static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, cons
   int ntop = 0;
   if (idx.nlev >= 2 && idx.lvl_n[1] <= kMapTopMax) ntop = (int)idx.lvl_n[1];
   const size_t smem = (size_t)ntop * sizeof(unsigned long long);
-  k_map_seg<T, kVec><<<(unsigned)blocks, 256, smem, st>>>((const T*)w, M, seg, idx, consts, (const u128*)Z, N, G, ntop,
-                                                          out);
+  k_map_seg<T, kVec><<<(unsigned)blocks, 256, smem, st>>>((const T*)w, M, seg, pre, idx, consts, (const u128*)Z, N, G,
+                                                          ntop, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegIndex& idx,
-                           const PathConsts* consts, const void* Z, long long N, int G, int* out, cudaStream_t st) {
+cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
+                           const SegIndex& idx, const PathConsts* consts, const void* Z, long long N, int G, int* out,
+                           cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  if (f32) return vec ? map_seg_t<float, true>(w, M, seg, idx, consts, Z, N, G, out, st)
-                      : map_seg_t<float, false>(w, M, seg, idx, consts, Z, N, G, out, st);
-  return vec ? map_seg_t<double, true>(w, M, seg, idx, consts, Z, N, G, out, st)
-             : map_seg_t<double, false>(w, M, seg, idx, consts, Z, N, G, out, st);
+  if (f32) return vec ? map_seg_t<float, true>(w, M, seg, pre, idx, consts, Z, N, G, out, st)
+                      : map_seg_t<float, false>(w, M, seg, pre, idx, consts, Z, N, G, out, st);
+  return vec ? map_seg_t<double, true>(w, M, seg, pre, idx, consts, Z, N, G, out, st)
+             : map_seg_t<double, false>(w, M, seg, pre, idx, consts, Z, N, G, out, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
                                                            unsigned long long inst, u128* __restrict__ Z,
                                                            u128* __restrict__ Ztot, PathConsts* consts,
                                                            TileDesc<u128>* desc, unsigned* ctr, int* status,
-                                                           int spin_limit) {
+                                                           int spin_limit, bool withhold_first) {
   __shared__ LogTab tab;
   __shared__ u128 s_wsum[kUWarps];
   __shared__ u128 s_woff[kUWarps];
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
     const u128 agg = shfl_v(wi, kUWarps - 1);
     u128 excl = {0ULL, 0ULL};
     if (tile == 0) {
-      if (lane == 0) lb_publish(desc, 0, agg, true);
+      if (lane == 0 && !withhold_first) lb_publish(desc, 0, agg, true);
     } else {
       if (lane == 0) lb_publish(desc, tile, agg, false);
       excl = lb_exclusive(desc, tile, lane, spin_limit, status);
@@ -156,15 +156,15 @@ cudaError_t init_log_table() {
 
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,
                                 void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
-                                int spin_limit, cudaStream_t st) {
+                                int spin_limit, bool withhold_first, cudaStream_t st) {
   const long long tiles = (ndraw + kUTile - 1) / kUTile;
   if (tiles <= 0) return cudaSuccess;
   if (f32)
     k_uniform_scan<true><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
-                                                                (TileDesc<u128>*)desc, ctr, status, spin_limit);
+                                                                (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first);
   else
     k_uniform_scan<false><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
-                                                                 (TileDesc<u128>*)desc, ctr, status, spin_limit);
+                                                                 (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first);
   return cudaGetLastError();
 }
 

@@ -260,19 +260,18 @@ def test_zero_sum_latches_status(g, h):
 
 
 def test_bounded_wait_times_out_and_context_survives(g, h):
-    """Fault injection on the host side: the first look-back tile withholds
-    its publication; every later tile's wait runs out after spin_limit polls.
-    (The segment-prefix scan chains tiles of 2048 segments of 512 weights.)"""
-    M = 3 * 2048 * 512 + 1000
-    w = workloads.weights_small(M, seed=2)
-    W = torch.empty(M, dtype=torch.float64, device="cuda")
-    g.rs_cumulative(h.h, dev(w), M, W, g.opts(spin_limit=200, debug_flags=1))
+    """Fault injection on the host side: the first look-back tile of the
+    spacing scan withholds its publication; every later tile's wait runs out
+    after spin_limit polls (tiles of 256 draws, so 40 tiles here)."""
+    N = 10_000
+    U = torch.empty(N, dtype=torch.float64, device="cuda")
+    g.rs_sorted_uniform(h.h, N, 5, 7, U, g.opts(spin_limit=200, debug_flags=1))
     assert h.status() == g.RS_ETIMEOUT
     # the context is still usable and a normal call is correct again
-    g.rs_cumulative(h.h, dev(w), M, W)
+    g.rs_sorted_uniform(h.h, N, 5, 7, U)
     assert h.status() == g.RS_OK
-    ref, _ = oracle.cumulative(w)
-    assert np.all(np.abs(host(W) - ref) <= REL_F64 * ref)
+    ref = oracle.sorted_uniform(N, 5, 7)
+    assert np.max(np.abs(host(U) - ref) / ref) <= 1e-13
 
 
 def test_host_argument_errors(g, h):
