@@ -55,7 +55,8 @@ typedef enum {
   RS_ECUDA = 3,       /* a CUDA runtime call failed */
   RS_ENONFINITE = 4,  /* a weight is negative, NaN or infinite (device-detected) */
   RS_EZEROSUM = 5,    /* the weights sum to zero (device-detected) */
-  RS_ETIMEOUT = 6     /* a bounded inter-block wait gave up (device-detected) */
+  RS_ETIMEOUT = 6,    /* a bounded inter-block wait gave up (device-detected) */
+  RS_ECAPACITY = 7    /* a size exceeds a fixed capacity (rs_sorted_uniform_static) */
 } rs_status;
 
 /* Inverse-CDF map used after the cumulative weights and uniforms exist. */
@@ -120,6 +121,50 @@ rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uin
  * arithmetic are used and the (hi+lo) result is returned widened. */
 rs_status rs_sorted_uniform(rs_handle* h, int64_t N, uint64_t seed, uint64_t instance, double* U_out,
                             const rs_opts* opts, void* stream);
+
+/* rs_sorted_uniform without any memory allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory once they are running -- for example a filter loop that
+ * reserved all of its memory at start-up and must keep a fixed footprint, or
+ * code that runs while the device is out of memory.  rs_sorted_uniform needs a
+ * handle, whose workspace grows by cudaMalloc when a call needs more; this
+ * call needs no handle and keeps its scratch (spacing sums, scan descriptors,
+ * per-call constants, about 1 MiB) in one fixed device array that is part of
+ * the loaded library.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Results are bit-identical to rs_sorted_uniform with the same N, seed,
+ * instance and precision (same kernels, same arithmetic).
+ *
+ *  N          number of uniforms, 0 <= N <= RS_STATIC_MAX_N (65,536).  A
+ *             larger N returns RS_ECAPACITY and enqueues nothing; use
+ *             rs_sorted_uniform for it.  N = 0 is a no-op.
+ *  precision  RS_F64 or RS_F32_COMP (as opts->prec of rs_sorted_uniform).
+ *  U_out      [N] binary64, device, 8-byte aligned, caller-owned; written.
+ *  status     optional device pointer to one int32, caller-owned.  A bounded
+ *             wait that runs out on the device stores RS_ETIMEOUT there if it
+ *             holds 0; the call never clears it.  NULL: such an error is not
+ *             reported.
+ *  stream     cudaStream_t; the call only enqueues work on it.
+ *
+ * Host-detected errors (N out of range, bad precision, NULL or misaligned
+ * U_out, a failed CUDA call) are returned at once: RS_EINVAL, RS_ECAPACITY or
+ * RS_ECUDA.
+ *
+ * Set-up: the first call on each device (the current device) looks up the
+ * scratch array's device address and uploads a 2 KB table used by the
+ * logarithm, synchronously; later calls on that device only enqueue work.
+ * Make that first call before any stream capture begins.
+ *
+ * Every call on one device uses the same scratch array, and each call first
+ * clears its scan counters there.  Calls whose GPU work can overlap (issued to
+ * different streams without ordering, or from different host threads) race on
+ * the scratch and give wrong results: issue them on one stream, or order them
+ * with events.  Host threads may call it concurrently only if their GPU work
+ * is ordered in that way. */
+#define RS_STATIC_MAX_N 65536
+rs_status rs_sorted_uniform_static(int64_t N, uint64_t seed, uint64_t instance, int32_t precision, double* U_out,
+                                   int32_t* status, void* stream);
 
 /* Eq. 3: cumulative weights.  w as in rs_resample_w; W_out [M] binary64,
  * written, non-decreasing, W_out[M-1] == 1 exactly. */

@@ -5,11 +5,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libgbresample.so")
 
-RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_EZEROSUM, RS_ETIMEOUT = range(7)
+RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_EZEROSUM, RS_ETIMEOUT, RS_ECAPACITY = range(8)
+RS_STATIC_MAX_N = 65536
 RS_MAP_DAC, RS_MAP_BINARY, RS_MAP_LINEAR = 0, 1, 2
 RS_F64, RS_F32_COMP = 0, 1
 _NAMES = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ENOMEM", 3: "RS_ECUDA", 4: "RS_ENONFINITE", 5: "RS_EZEROSUM",
-          6: "RS_ETIMEOUT"}
+          6: "RS_ETIMEOUT", 7: "RS_ECAPACITY"}
 
 
 class ResampleError(RuntimeError):
@@ -54,6 +55,7 @@ def lib():
             "rs_resample_w": (_ST, [_P, _P, _I64, _I64, _U64, _U64, _P, _P, _OPTS, _P]),
             "rs_resample_W": (_ST, [_P, _P, _I64, _I64, _U64, _U64, _P, _OPTS, _P]),
             "rs_sorted_uniform": (_ST, [_P, _I64, _U64, _U64, _P, _OPTS, _P]),
+            "rs_sorted_uniform_static": (_ST, [_I64, _U64, _U64, _I32, _P, _P, _P]),
             "rs_cumulative": (_ST, [_P, _P, _I64, _P, _OPTS, _P]),
             "rs_map": (_ST, [_P, _P, _I64, _P, _I64, _P, _OPTS, _P]),
             "rs_philox": (_ST, [_P, _U64, _U64, _U64, _I64, _P, _P]),
@@ -133,6 +135,12 @@ def rs_resample_W(h, W, M, N, seed, instance, out_idx, o=None, stream=None):
 
 def rs_sorted_uniform(h, N, seed, instance, U_out, o=None, stream=None):
     _check(h, lib().rs_sorted_uniform(h, N, seed, instance, _ptr(U_out), _opt(o), _stream(stream)))
+
+
+def rs_sorted_uniform_static(N, seed, instance, U_out, precision=RS_F64, status=None, stream=None):
+    """Allocation-free sorted uniforms; returns the rs_status code (no handle,
+    so no error text)."""
+    return lib().rs_sorted_uniform_static(N, seed, instance, precision, _ptr(U_out), _ptr(status), _stream(stream))
 
 
 def rs_cumulative(h, w, M, W_out, o=None, stream=None):
