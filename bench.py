@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the map-only and e2e sub-measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the sub-measurements (e2e, map only, batched, bootstrap, stress)")
     return ap.parse_args()
 
 
@@ -279,6 +280,12 @@ def run_ours(args):
         line["e2e"] = e2e_measure(g, h, wl, dev, stream, min(K, 100), inst)
         if ws == 1:
             line["map_only"] = map_only(g, h, wl, dev, stream)
+            del wd, flush, graph
+            torch.cuda.empty_cache()
+            line["batched"] = batched_measure(g, h, dev, stream, hbm)
+            torch.cuda.empty_cache()
+            line["bootstrap"] = single_measure(g, h, dev, stream, "bootstrap", hbm)
+            line["stress"] = single_measure(g, h, dev, stream, "stress", hbm)
     else:
         line["e2e"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -339,6 +346,119 @@ def map_only(g, h, wl, dev, stream, K=50):
             torch.cuda.synchronize()
             ms = statistics.median(a.elapsed_time(b) for a, b in ev)
             res[name] = {"us_per_call": ms * 1e3, "particles_per_s": N / (ms * 1e-3)}
+    return res
+
+
+def _time_calls(fn, stream, reps, warm=2):
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warm):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def batched_measure(g, h, dev, stream, hbm, reps=20):
+    """8192 EnGMF-shaped instances (N_k ~ U{64..2048}, P_k ~ U{1..64},
+    M_k = N_k P_k, binary32 weights): the persistent batched launch (autotuned,
+    replayed as a CUDA graph) against one binary64 rs_resample_w per instance
+    (plain launches, and the same loop captured in a graph), plus the binary32
+    cumulative-weight error against binary64 on a sample of instances."""
+    import torch
+    wl = workloads.make("batched")
+    w32, woff, roff, K = wl.w, wl.woff, wl.roff, wl.info["K"]
+    sumM, sumN = int(woff[-1]), int(roff[-1])
+    wd = torch.from_numpy(w32).to(dev)
+    wo, ro = torch.from_numpy(woff).to(dev), torch.from_numpy(roff).to(dev)
+    out = torch.empty(sumN, dtype=torch.int32, device=dev)
+    best = g.rs_autotune_batched(h.h, wd, wo, ro, K, wl.seed, out, woff, roff, stream=stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        g.rs_resample_batched(h.h, wd, wo, ro, K, wl.seed, out, woff, roff, stream=stream)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=stream):
+        g.rs_resample_batched(h.h, wd, wo, ro, K, wl.seed, out, woff, roff, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms32 = _time_calls(graph.replay, stream, reps)
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the batched run")
+    del graph
+    # binary64 comparison: the same weights widened, one rs_resample_w per instance
+    w64 = wd.double()
+    del wd
+    o64 = g.opts(prec=g.RS_F64)
+    f64 = lambda s=None: g.rs_resample_batched(h.h, w64, wo, ro, K, wl.seed, out, woff, roff, o64,  # noqa: E731
+                                                stream=s or stream)
+    ms64 = _time_calls(f64, stream, 2, warm=1)
+    g64 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g64, stream=stream):
+        f64(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms64g = _time_calls(g64.replay, stream, 3, warm=1)
+    del g64
+    # binary32-compensated W against binary64 W on 64 instances
+    rng = np.random.default_rng(0)
+    err = 0.0
+    for k in rng.choice(K, size=64, replace=False):
+        a, b = int(woff[k]), int(woff[k + 1])
+        W32 = torch.empty(b - a, dtype=torch.float64, device=dev)
+        W64 = torch.empty(b - a, dtype=torch.float64, device=dev)
+        w32k = torch.from_numpy(w32[a:b]).to(dev)
+        g.rs_cumulative(h.h, w32k, b - a, W32, g.opts(prec=g.RS_F32_COMP), stream=stream)
+        g.rs_cumulative(h.h, w64[a:b].contiguous(), b - a, W64, g.opts(prec=g.RS_F64), stream=stream)
+        torch.cuda.synchronize()
+        err = max(err, float((W32 - W64).abs().max().item()))
+    bytes32 = 4 * sumM + 4 * sumN
+    return {"workload": "K=8192 instances, N_k~U{64..2048}, P_k~U{1..64}, M_k=N_k*P_k, binary32 exp(l-max), "
+                        "l~Normal(0,1.5^2)", "K": K, "sum_M": sumM, "sum_N": sumN,
+            "tuned": {"tile_threads": best.tile_threads, "leaf_L": best.leaf_L},
+            "f32_batched_graph_us": ms32 * 1e3, "f32_particles_per_s": sumN / (ms32 * 1e-3),
+            "f32_GBps": bytes32 / (ms32 * 1e-3) / 1e9, "f32_frac_of_hbm": bytes32 / (ms32 * 1e-3) / 1e9 / hbm,
+            "f64_per_instance_launches_us": ms64 * 1e3, "f64_per_instance_graph_us": ms64g * 1e3,
+            "speedup_vs_f64_launches": ms64 / ms32, "speedup_vs_f64_graph": ms64g / ms32,
+            "max_abs_W_err_f32comp_vs_f64": err, "W_err_bound": 4 * 2.0 ** -23, "err_sample": "64 instances"}
+
+
+def single_measure(g, h, dev, stream, name, hbm, reps=20):
+    """rs_resample_w on the bootstrap (M = N) or precision-stress instance, in
+    binary64 and, for the stress case, compensated binary32 with the error
+    report (max |W32c - W64|, max |U32c - U64|, index mismatches)."""
+    import torch
+    wl = workloads.make(name)
+    M, N, seed = wl.M, wl.N, wl.seed
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    res = {"M": M, "N": N}
+    variants = [("f64", torch.from_numpy(wl.w).to(dev), g.RS_F64)]
+    if wl.w32 is not None:
+        variants.append(("f32comp", torch.from_numpy(wl.w32).to(dev), g.RS_F32_COMP))
+    outs = {}
+    for tag, wd, prec in variants:
+        o = g.opts(prec=prec)
+        ms = _time_calls(lambda: g.rs_resample_w(h.h, wd, M, N, seed, 0, out, None, o, stream=stream), stream, reps)
+        bytes_ = wd.element_size() * M + 4 * N
+        res[tag] = {"us_per_call": ms * 1e3, "particles_per_s": N / (ms * 1e-3),
+                    "GBps": bytes_ / (ms * 1e-3) / 1e9, "frac_of_hbm": bytes_ / (ms * 1e-3) / 1e9 / hbm}
+        outs[tag] = out.clone()
+    if len(variants) == 2:
+        W64 = torch.empty(M, dtype=torch.float64, device=dev)
+        W32 = torch.empty(M, dtype=torch.float64, device=dev)
+        g.rs_cumulative(h.h, variants[0][1], M, W64, g.opts(prec=g.RS_F64), stream=stream)
+        g.rs_cumulative(h.h, variants[1][1], M, W32, g.opts(prec=g.RS_F32_COMP), stream=stream)
+        U64 = torch.empty(N, dtype=torch.float64, device=dev)
+        U32 = torch.empty(N, dtype=torch.float64, device=dev)
+        g.rs_sorted_uniform(h.h, N, seed, 0, U64, g.opts(prec=g.RS_F64), stream=stream)
+        g.rs_sorted_uniform(h.h, N, seed, 0, U32, g.opts(prec=g.RS_F32_COMP), stream=stream)
+        torch.cuda.synchronize()
+        res["max_abs_W_err_f32comp_vs_f64"] = float((W32 - W64).abs().max().item())
+        res["max_abs_U_err_f32comp_vs_f64"] = float((U32 - U64).abs().max().item())
+        res["index_mismatches_f32comp_vs_f64"] = int((outs["f32comp"] != outs["f64"]).sum().item())
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the %s run" % name)
     return res
 
 

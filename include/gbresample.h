@@ -79,15 +79,21 @@ typedef enum { RS_F64 = 0, RS_F32_COMP = 1 } rs_precision;
 typedef struct {
   int32_t algo;        /* rs_map_algo (default RS_MAP_DAC) */
   int32_t prec;        /* rs_precision (default RS_F64) */
-  int32_t leaf_L;      /* DaC: samples per leaf (power of two 1..1024; 0 = choose from M/N) */
-  int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 4096) */
+  int32_t leaf_L;      /* DaC: samples per leaf (power of two 1..1024; 0 = choose from M/N).
+                          rs_resample_batched: the leaf threshold - a segment holding at
+                          most leaf_L samples is resolved by a warp-wide count over its
+                          512 prefixes (linear walk), a fuller one by per-sample binary
+                          search (0 = the autotuned or default value) */
+  int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 512) */
   int32_t spin_limit;  /* bounded-wait iterations before RS_ETIMEOUT (0 = default) */
   int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of every
                           look-back scan of the call (spacings, tile prefixes)
                           withholds its publication, so every later tile's bounded
                           wait runs out and RS_ETIMEOUT is latched (results are then
                           unspecified).  Nothing faults. */
-  int32_t reserved[2]; /* must be zero */
+  int32_t tile_threads; /* rs_resample_batched: threads per CTA, 128, 256 or 512
+                           (0 = the autotuned or default value); ignored elsewhere */
+  int32_t reserved;    /* must be zero */
 } rs_opts;
 
 /* Create a handle bound to the CUDA device current on the calling thread.
@@ -182,20 +188,41 @@ rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int6
 rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t first, int64_t n, uint64_t* out,
                     void* stream);
 
-/* K independent instances in one launch sequence (the many-filter setting of
- * Sec. I: M_k = N_k * P_k weights per filter).  Instance k owns
- * w[w_off[k] .. w_off[k+1]) and out_idx[r_off[k] .. r_off[k+1]) and draws from
- * the Philox stream (seed, instance = k).
+/* K independent instances (the many-filter setting of Sec. I: M_k = N_k * P_k
+ * weights per filter).  Instance k owns w[w_off[k] .. w_off[k+1]) and
+ * out_idx[r_off[k] .. r_off[k+1]) and draws from the Philox stream
+ * (seed, instance = k); its indices equal those of rs_resample_w on that
+ * instance alone (same precision), bit for bit.
  *  w      [w_off[K]] binary32 (RS_F32_COMP, the default for this call when
- *         opts is NULL) or binary64 (RS_F64) weights.
+ *         opts is NULL) or binary64 (RS_F64) weights; 4- resp. 8-byte aligned.
  *  w_off, r_off  [K+1] int64 DEVICE arrays, non-decreasing, starting at 0;
  *         every instance needs M_k >= 1 unless N_k = 0.
- *  h_w_off, h_r_off  optional HOST copies of the same offsets (may be NULL);
- *         when given, the host orders instances by size without a device read.
- *  out_idx [r_off[K]] int32 indices, local to each instance, written. */
+ *  h_w_off, h_r_off  optional HOST copies of the same offsets (may be NULL).
+ *         When NULL the call copies the offsets to the host and synchronises
+ *         the stream (not allowed during stream capture); when given it reads
+ *         nothing back from the device.
+ *  out_idx [r_off[K]] int32 indices, local to each instance, written.
+ * RS_F32_COMP: one persistent launch processes every instance of at most
+ * 262,144 weights (one CTA per instance, taken from an atomic queue in order
+ * of decreasing M_k); larger instances go through the single-instance path
+ * first, on the same stream.  RS_F64: one rs_resample_w per instance.
+ * opts->tile_threads and opts->leaf_L select the CTA size and the leaf
+ * threshold; 0 takes the values rs_autotune_batched stored in the handle, or
+ * defaults (256, 4). */
 rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
                               const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
                               const rs_opts* opts, void* stream);
+
+/* Autotuner of rs_resample_batched: runs the call (same arguments, which must
+ * be valid; outputs are written) for each candidate CTA size {128, 256, 512}
+ * and leaf threshold {1, 4, 32}, times each with CUDA events on `stream`
+ * (one warm-up, three timed runs), keeps the fastest in the handle for later
+ * calls with zero tile_threads / leaf_L, and writes it to *best (may be NULL):
+ * best->tile_threads, best->leaf_L, best->prec.  Synchronises the stream; call
+ * it before any stream capture. */
+rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
+                              const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
+                              const rs_opts* opts, rs_opts* best, void* stream);
 
 /* Synchronise `stream`, return the device status latched since the previous
  * call (RS_OK if none) and clear it. */

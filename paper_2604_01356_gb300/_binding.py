@@ -22,11 +22,11 @@ class ResampleError(RuntimeError):
 class rs_opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("prec", ctypes.c_int32), ("leaf_L", ctypes.c_int32),
                 ("stage_max", ctypes.c_int32), ("spin_limit", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("tile_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
-def opts(algo=RS_MAP_DAC, prec=RS_F64, leaf_L=0, stage_max=0, spin_limit=0, debug_flags=0):
-    return rs_opts(algo, prec, leaf_L, stage_max, spin_limit, debug_flags)
+def opts(algo=RS_MAP_DAC, prec=RS_F64, leaf_L=0, stage_max=0, spin_limit=0, debug_flags=0, tile_threads=0):
+    return rs_opts(algo, prec, leaf_L, stage_max, spin_limit, debug_flags, tile_threads)
 
 
 _lib = None
@@ -60,6 +60,7 @@ def lib():
             "rs_map": (_ST, [_P, _P, _I64, _P, _I64, _P, _OPTS, _P]),
             "rs_philox": (_ST, [_P, _U64, _U64, _U64, _I64, _P, _P]),
             "rs_resample_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _P]),
+            "rs_autotune_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _OPTS, _P]),
             "rs_trace_enable": (_ST, [_P, ctypes.c_int]),
             "rs_trace_collect": (_ST, [_P, ctypes.c_int]),
             "rs_trace_report": (_ST, [_P, ctypes.c_char_p, _I64]),
@@ -155,13 +156,30 @@ def rs_philox(h, seed, instance, first, n, out, stream=None):
     _check(h, lib().rs_philox(h, seed, instance, first, n, _ptr(out), _stream(stream)))
 
 
+def _host_offsets(a):
+    import numpy as np
+    return None if a is None else np.ascontiguousarray(a, dtype=np.int64)
+
+
 def rs_resample_batched(h, w, w_off, r_off, K, seed, out_idx, h_w_off=None, h_r_off=None, o=None, stream=None):
     """w_off, r_off: device int64 tensors [K+1]; h_w_off, h_r_off: optional host
-    int64 numpy arrays with the same offsets."""
-    hw = h_w_off.ctypes.data if h_w_off is not None else None
-    hr = h_r_off.ctypes.data if h_r_off is not None else None
-    _check(h, lib().rs_resample_batched(h, _ptr(w), _ptr(w_off), _ptr(r_off), K, hw, hr, seed, _ptr(out_idx), _opt(o),
+    int64 arrays with the same offsets."""
+    hw, hr = _host_offsets(h_w_off), _host_offsets(h_r_off)
+    _check(h, lib().rs_resample_batched(h, _ptr(w), _ptr(w_off), _ptr(r_off), K,
+                                        None if hw is None else hw.ctypes.data,
+                                        None if hr is None else hr.ctypes.data, seed, _ptr(out_idx), _opt(o),
                                         _stream(stream)))
+
+
+def rs_autotune_batched(h, w, w_off, r_off, K, seed, out_idx, h_w_off=None, h_r_off=None, o=None, stream=None):
+    """Runs the tuner; returns the chosen rs_opts (tile_threads, leaf_L, prec)."""
+    hw, hr = _host_offsets(h_w_off), _host_offsets(h_r_off)
+    best = rs_opts()
+    _check(h, lib().rs_autotune_batched(h, _ptr(w), _ptr(w_off), _ptr(r_off), K,
+                                        None if hw is None else hw.ctypes.data,
+                                        None if hr is None else hr.ctypes.data, seed, _ptr(out_idx), _opt(o),
+                                        ctypes.byref(best), _stream(stream)))
+    return best
 
 
 def rs_trace_enable(h, on=True):

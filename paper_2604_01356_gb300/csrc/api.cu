@@ -29,6 +29,7 @@ struct rs_handle {
   cudaStream_t side = nullptr;    // second stream for work independent of the weights pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool tracing = false;
+  int tuned_threads = 0, tuned_leaf = 0;  // rs_autotune_batched's choice (0: none yet)
   std::vector<rs_trace_pair> pending;
   std::vector<rs_trace_total> totals;
 };
@@ -104,6 +105,7 @@ struct Opts {
   int stage_max = kStageCap;
   int spin = kDefaultSpin;
   int debug = 0;
+  int threads = 0;
 };
 
 rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec) {
@@ -116,8 +118,10 @@ rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec)
       return fail(h, RS_EINVAL, "opts.leaf_L must be 0 or a power of two <= 1024");
     if (o->stage_max < 0) return fail(h, RS_EINVAL, "opts.stage_max negative");
     if (o->spin_limit < 0) return fail(h, RS_EINVAL, "opts.spin_limit negative");
-    for (int i = 0; i < 2; ++i)
-      if (o->reserved[i]) return fail(h, RS_EINVAL, "opts.reserved must be zero");
+    if (o->reserved) return fail(h, RS_EINVAL, "opts.reserved must be zero");
+    if (o->tile_threads != 0 && o->tile_threads != 128 && o->tile_threads != 256 && o->tile_threads != 512)
+      return fail(h, RS_EINVAL, "opts.tile_threads must be 0, 128, 256 or 512");
+    r.threads = o->tile_threads;
     if (o->debug_flags & ~1) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
     r.debug = o->debug_flags;
     r.algo = o->algo;
@@ -602,6 +606,9 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
   if (K < 0) return fail(h, RS_EINVAL, "K must be >= 0");
   if (K == 0) return RS_OK;
   if (!w || !w_off || !r_off) return fail(h, RS_EINVAL, "w, w_off and r_off must be non-NULL");
+  const bool f32 = o.prec == RS_F32_COMP;
+  if (!aligned(w, f32 ? 4 : 8)) return fail(h, RS_EINVAL, "w must be aligned to its element size");
+  if (!aligned(w_off, 8) || !aligned(r_off, 8)) return fail(h, RS_EINVAL, "w_off and r_off must be 8-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   std::vector<int64_t> wo, ro;
   if (h_w_off && h_r_off) {
@@ -621,16 +628,94 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
     if (Nk > 0 && Mk < 1) return fail(h, RS_EINVAL, "an instance with samples needs at least one weight");
     if (Mk > kMaxLen || Nk > kMaxLen) return fail(h, RS_EINVAL, "instance too large");
   }
-  const size_t esz = o.prec == RS_F32_COMP ? 4 : 8;
+  if (ro[K] > 0 && (!out_idx || !aligned(out_idx, 4))) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  const size_t esz = f32 ? 4 : 8;
   rs_opts one;
   memset(&one, 0, sizeof(one));
   one.prec = o.prec;
   one.spin_limit = o.spin;
+  // instances the persistent kernel does not take: every one in binary64,
+  // the large ones in binary32
   for (int32_t k = 0; k < K; ++k) {
     const long long Mk = wo[k + 1] - wo[k], Nk = ro[k + 1] - ro[k];
     if (Nk == 0) continue;
+    if (f32 && (Mk + kSegLen - 1) / kSegLen <= kBMaxSeg) continue;
     const void* wk = static_cast<const char*>(w) + (size_t)wo[k] * esz;
     if ((s = rs_resample_w(h, wk, Mk, Nk, seed, (uint64_t)k, out_idx + ro[k], nullptr, &one, stream))) return s;
+  }
+  if (!f32) return RS_OK;
+  Layout L;
+  const size_t o_queue = L.take(256);
+  const size_t o_order = L.take((size_t)K * sizeof(int));
+  if ((s = ensure_ws(h, L.off))) return s;
+  const int threads = o.threads ? o.threads : (h->tuned_threads ? h->tuned_threads : 256);
+  const int leaf = o.leaf_L ? o.leaf_L : (h->tuned_leaf ? h->tuned_leaf : 4);
+  {
+    RS_TRACE(h, "batched_order", st);
+    RS_CK(h, cudaMemsetAsync(at<unsigned>(h, o_queue), 0, 256, st));
+    RS_CK(h, launch_batched_order(reinterpret_cast<const long long*>(w_off), K, at<int>(h, o_order), st));
+  }
+  {
+    RS_TRACE(h, "batched", st);
+    RS_CK(h, launch_batched_f32(static_cast<const float*>(w), reinterpret_cast<const long long*>(w_off),
+                                reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, threads, leaf,
+                                out_idx, at<unsigned>(h, o_queue), h->status, st));
+  }
+  return RS_OK;
+}
+
+rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
+                              const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
+                              const rs_opts* opts, rs_opts* best, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F32_COMP))) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  static const int kThreadsC[3] = {128, 256, 512};
+  static const int kLeafC[3] = {1, 4, 32};
+  rs_opts c;
+  memset(&c, 0, sizeof(c));
+  c.prec = o.prec;
+  c.spin_limit = opts ? opts->spin_limit : 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RS_CK(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
+  }
+  float best_ms = -1.0f;
+  int bt = 256, bl = 4;
+  for (int a = 0; a < 3 && !s; ++a) {
+    for (int b = 0; b < 3 && !s; ++b) {
+      c.tile_threads = kThreadsC[a];
+      c.leaf_L = kLeafC[b];
+      if ((s = rs_resample_batched(h, w, w_off, r_off, K, h_w_off, h_r_off, seed, out_idx, &c, stream))) break;
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3 && !s; ++r)
+        s = rs_resample_batched(h, w, w_off, r_off, K, h_w_off, h_r_off, seed, out_idx, &c, stream);
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess && !s) s = cuda_fail(h, e, "autotune timing");
+      if (!s && (best_ms < 0.0f || ms < best_ms)) {
+        best_ms = ms;
+        bt = c.tile_threads;
+        bl = c.leaf_L;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  h->tuned_threads = bt;
+  h->tuned_leaf = bl;
+  if (best) {
+    memset(best, 0, sizeof(*best));
+    best->prec = o.prec;
+    best->tile_threads = bt;
+    best->leaf_L = bl;
   }
   return RS_OK;
 }

@@ -101,6 +101,13 @@ cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const
 cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
                            const SegIndex& idx, const PathConsts* consts, const void* Z, long long N, int G, int* out,
                            cudaStream_t st);
+// --- batched persistent path (K instances, one CTA per instance) ----------
+constexpr int kBMaxSeg = 512;     // segments of the largest instance a CTA takes (M_k <= 262,144)
+constexpr int kSortMax = 16384;   // batches up to this size are ordered by M_k on the device
+cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cudaStream_t st);
+cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
+                               unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
+                               int* status, cudaStream_t st);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

@@ -22,8 +22,7 @@
 // Comparisons on a given binary64 W are exact: values are compared through
 // their total-order integer keys, which agree with IEEE comparison for every
 // non-NaN value, so all three maps return bit-identical indices.
-#include "common.cuh"
-#include "internal.h"
+#include "seg_common.cuh"
 
 namespace gbr {
 
@@ -34,44 +33,8 @@ __device__ __forceinline__ long long ldkey(const double* __restrict__ p) {
 // ---------------------------------------------------------------------------
 // Map from weights, over the segment records of the first weights pass.
 // ---------------------------------------------------------------------------
-template <typename T, bool kVec>
-__device__ __forceinline__ void load_blocked(const T* __restrict__ w, long long base, long long M, int lane,
-                                             typename FixedTraits<T>::Bits (&b)[kSegV]) {
-  using Bits = typename FixedTraits<T>::Bits;
-  const long long e0 = base + (long long)lane * kSegV;
-  if (kVec && e0 + kSegV <= M) {
-    if (sizeof(T) == 8) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(w + e0 + 2 * i));
-        b[2 * i] = (Bits)v.x;
-        b[2 * i + 1] = (Bits)v.y;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + e0 + 4 * i));
-        b[4 * i] = (Bits)v.x;
-        b[4 * i + 1] = (Bits)v.y;
-        b[4 * i + 2] = (Bits)v.z;
-        b[4 * i + 3] = (Bits)v.w;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kSegV; ++i) {
-      const long long e = e0 + i;
-      if (sizeof(T) == 8) b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e)) : (Bits)0;
-      else b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e)) : (Bits)0;
-    }
-  }
-}
-
 __device__ __forceinline__ u128 seg_pre(const SegPre* __restrict__ pre, long long s) {
   return u128{__ldcg(&pre[s].lo), __ldcg(&pre[s].hi)};
-}
-__device__ __forceinline__ bool u128_lt(const u128& a, const u128& b) {
-  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 __device__ __forceinline__ xf ld_consts_xf(const unsigned long long* p) {
   return {__ldcg(p), __ldcg(p + 1), (long long)__ldcg(p + 2)};
@@ -154,7 +117,7 @@ __device__ __forceinline__ int head_count(const double* __restrict__ w, long lon
   shr128(rh, rl, 25);
   const long long ue = rem.e + 25;
   Tr::Bits b[kSegV];
-  load_blocked<double, kVec>(w, base, M, lane, b);
+  load_seg_blocked<double, kVec>(w, base, M, lane, b);
   u128 run = {0ULL, 0ULL};
 #pragma unroll
   for (int i = 0; i < kSegV; ++i) run = sat_add(run, head_val(b[i], ue));
@@ -179,37 +142,6 @@ __device__ __forceinline__ int head_count(const double* __restrict__ w, long lon
 template <bool kVec>
 __device__ __forceinline__ int head_count(const float*, long long, long long, const xf&, int) {
   return 0;  // binary32 weights never need it: their grid is finer than the tolerance
-}
-
-// K = ceil(rem / 2^sh) clamped to [1, F]: the segment-grid target of a key
-// that lies rem grid units above the segment's start.
-__device__ __forceinline__ unsigned long long ceil_units(u128 rem, int sh, unsigned long long F) {
-  if (u128_is_zero(rem)) return 1;
-  unsigned long long K;
-  if (sh >= 0) {
-    if (sh >= 128) {
-      K = 1;
-    } else {
-      uint64_t ah = 0, al = 0;  // 2^sh - 1
-      if (sh >= 64) {
-        ah = (sh == 64) ? 0 : ((1ULL << (sh - 64)) - 1);
-        al = ~0ULL;
-      } else {
-        al = (1ULL << sh) - 1;
-      }
-      uint64_t nl = rem.lo + al;
-      uint64_t nh = rem.hi + ah + (nl < rem.lo ? 1ULL : 0ULL);
-      shr128(nh, nl, sh);
-      K = nh ? F : nl;
-    }
-  } else {
-    // rem * 2^-sh; anything at or above 2^63 is past F anyway
-    const int ls = -sh;
-    K = (rem.hi || ls >= 63 || (rem.lo >> (63 - ls))) ? F : (rem.lo << ls);
-  }
-  if (K > F) K = F;
-  if (K < 1) K = 1;
-  return K;
 }
 
 template <typename T, bool kVec>
@@ -254,26 +186,7 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
     for (int q = 0; q < kSegV; ++q) pref[q] = 0;
     for (long long i = i0; i < i1; ++i) {
       const u128 z = (g == gw0 && i == i0) ? z_first : Z[i];
-      // key = U_i * S in grid units, rounded up: ceil(Z_i * (S / Z_{N+1}))
-      const xf kx = xf_mul_u128(s_c, z);
-      u128 key = {0ULL, 0ULL};
-      if (!xf_zero(kx)) {
-        uint64_t kh = kx.hi, kl = kx.lo;
-        if (kx.e >= 0) {
-          shl128(kh, kl, kx.e > 1 ? 1 : (int)kx.e);  // key <= S < 2^126: e <= 1
-        } else {
-          const int r = kx.e < -127 ? 128 : (int)(-kx.e);
-          uint64_t th = kh, tl = kl;
-          shr128(th, tl, r);
-          uint64_t bh = th, bl = tl;
-          shl128(bh, bl, r < 128 ? r : 0);
-          const bool frac = r >= 128 ? true : (bh != kh || bl != kl);
-          kh = th;
-          kl = tl + (frac ? 1ULL : 0ULL);
-          if (kl < tl) ++kh;
-        }
-        key = u128{kl, kh};
-      }
+      const u128 key = map_key(s_c, z);  // ceil(U_i * S) in grid units
       if (s < 0 || !(u128_lt(Ps, key) && !u128_lt(Pn, key))) {
         const unsigned long long kb = u128_key(key);
         long long ns = -1;
@@ -289,7 +202,7 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
         s = ns;
         // the segment's record, prefixes and weights are independent loads
         Bits b[kSegV];
-        load_blocked<T, kVec>(w, s * kSeg, M, lane, b);
+        load_seg_blocked<T, kVec>(w, s * kSeg, M, lane, b);
         const SegRec r = seg[s];
         Ps = seg_pre(pre, s);
         Pn = (s + 1 < nseg) ? seg_pre(pre, s + 1) : s_S;
@@ -298,17 +211,7 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
         F = r.F;
         const xf Px = xf_make(Ps.hi, Ps.lo, 0);
         head = sizeof(T) == 8 && (xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50);
-        if (!head) {
-          uint64_t run = 0;
-#pragma unroll
-          for (int q = 0; q < kSegV; ++q) {
-            run += Tr::fixed(b[q], (uint32_t)r.E);
-            pref[q] = run;
-          }
-          const uint64_t off = warp_incl_scan_u64(run, lane) - run;
-#pragma unroll
-          for (int q = 0; q < kSegV; ++q) pref[q] += off;
-        }
+        if (!head) seg_prefixes<T>(b, (uint32_t)r.E, lane, pref);
       }
       const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
       int cnt;

@@ -12,8 +12,7 @@
 // to binary64 (monotone in Z_i by construction).
 #include <cmath>
 
-#include "common.cuh"
-#include "internal.h"
+#include "seg_common.cuh"
 
 namespace gbr {
 
@@ -23,13 +22,12 @@ constexpr int kUThreads = 256;
 constexpr int kUWarps = kUThreads / kWarp;
 constexpr int kUItems = 1;  // one draw per thread (short dependent chains)
 static_assert(kUThreads * kUItems == kUTile, "uniform tile");
-constexpr int kZFrac = 88;  // spacing grid 2^-88
 
 // 1/Z_{N+1} as an xf, once per call by the thread that produced Z_{N+1}
 // (binary64-pair division, out of line; this kernel runs beside the weights
 // pass, so the cost is off the critical path).
 __device__ __noinline__ void store_recip(unsigned long long* dst, u128 t) {
-  const xf r = xf_div(xf_from_u64(1, 0), xf_make(t.hi, t.lo, 0));
+  const xf r = recip_total(t);
   dst[0] = r.lo;
   dst[1] = r.hi;
   dst[2] = (unsigned long long)r.e;
@@ -59,26 +57,13 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
 
   u128 pre[kUItems];  // thread-local inclusive prefixes
   u128 run = {0ULL, 0ULL};
-  uint64_t words[4];
   // each thread evaluates the Philox block of its own draw (four neighbouring
   // threads share a block; recomputing it is cheaper than the shuffles' wait)
-  philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
-  const unsigned wq = (unsigned)(k0 & 3);
-  const uint64_t word = wq == 0 ? words[0] : wq == 1 ? words[1] : wq == 2 ? words[2] : words[3];
+  const uint64_t word = philox_word(seed, inst, k0);
 #pragma unroll
   for (int q = 0; q < kUItems; ++q) {
     const long long k = k0 + q;
-    u128 f = {0ULL, 0ULL};
-    if (k < ndraw) {
-      if (F32) {
-        const float v = __int2float_rn((int)(2u * (uint32_t)(word >> 41) + 1u)) * 0x1p-24f;  // exact
-        f = f_to_fixed128<kZFrac>(-logf(v));
-      } else {
-        const df z = neg_log_draw(2ULL * (word >> 12) + 1ULL, 53, tab);
-        f = f_to_fixed128<kZFrac>(z.hi);
-        f = (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
-      }
-    }
+    const u128 f = k < ndraw ? spacing_fixed<F32>(word, &tab) : u128{0ULL, 0ULL};
     run = u128_add(run, f);
     pre[q] = run;
   }

@@ -18,8 +18,7 @@
 //           the weights and writes W_j = (P_s + F_j unit_s) / S rounded to
 //           binary64 by integer operations, clamped so that W is
 //           non-decreasing and W_M = 1.
-#include "common.cuh"
-#include "internal.h"
+#include "seg_common.cuh"
 
 namespace gbr {
 
@@ -27,90 +26,6 @@ constexpr int kWThreads = 256;
 constexpr int kWWarps = kWThreads / kWarp;
 static_assert(kWWarps == kSegsPerTile, "a reduce block is one tile of segments");
 static_assert(kSegsPerTile == 8, "tile size");
-
-// Striped (coalesced) load of one segment: lane holds elements
-//   binary64: 2*lane + 64*i + {0,1},   i < 8
-//   binary32: 4*lane + 128*i + {0..3}, i < 4
-// Missing elements of a ragged last segment read as +0.
-template <typename T, bool kVec>
-__device__ __forceinline__ void load_seg_striped(const T* __restrict__ w, long long base, long long M, int lane,
-                                                 typename FixedTraits<T>::Bits (&b)[kSegV]) {
-  using Bits = typename FixedTraits<T>::Bits;
-  const bool full = base + kSeg <= M;
-  if (sizeof(T) == 8) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const long long e = base + 2 * lane + 64 * i;
-      if (kVec && full) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(w + e));
-        b[2 * i] = (Bits)v.x;
-        b[2 * i + 1] = (Bits)v.y;
-      } else {
-        b[2 * i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e)) : (Bits)0;
-        b[2 * i + 1] = e + 1 < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e + 1)) : (Bits)0;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const long long e = base + 4 * lane + 128 * i;
-      if (kVec && full) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + e));
-        b[4 * i] = (Bits)v.x;
-        b[4 * i + 1] = (Bits)v.y;
-        b[4 * i + 2] = (Bits)v.z;
-        b[4 * i + 3] = (Bits)v.w;
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          b[4 * i + q] = e + q < M ? (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e + q)) : (Bits)0;
-      }
-    }
-  }
-}
-
-// Lane-major load (lane holds 16 consecutive elements 16*lane + i), used
-// where within-segment order matters (prefixes).
-template <typename T, bool kVec>
-__device__ __forceinline__ void load_seg_blocked(const T* __restrict__ w, long long base, long long M, int lane,
-                                                 typename FixedTraits<T>::Bits (&b)[kSegV]) {
-  using Bits = typename FixedTraits<T>::Bits;
-  const long long e0 = base + (long long)lane * kSegV;
-  const bool full = e0 + kSegV <= M;
-  if (kVec && full) {
-    if (sizeof(T) == 8) {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(w + e0 + 2 * i));
-        b[2 * i] = (Bits)v.x;
-        b[2 * i + 1] = (Bits)v.y;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + e0 + 4 * i));
-        b[4 * i] = (Bits)v.x;
-        b[4 * i + 1] = (Bits)v.y;
-        b[4 * i + 2] = (Bits)v.z;
-        b[4 * i + 3] = (Bits)v.w;
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < kSegV; ++i) {
-      const long long e = e0 + i;
-      if (sizeof(T) == 8) b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e)) : (Bits)0;
-      else b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e)) : (Bits)0;
-    }
-  }
-}
-
-__device__ __forceinline__ void st_xf(unsigned long long* p, const xf& v) {
-  p[0] = v.lo;
-  p[1] = v.hi;
-  p[2] = (unsigned long long)v.e;
-}
-__device__ __forceinline__ xf ld_xf(const unsigned long long* p) { return {p[0], p[1], (long long)p[2]}; }
 
 // ---- reduce: exact segment sums ------------------------------------------
 // One warp per segment; each block of 8 warps also records the largest
@@ -127,27 +42,8 @@ __global__ void __launch_bounds__(kWThreads, 4) k_w_reduce(const T* __restrict__
   uint32_t E = 0;
   if (s < nseg) {
     const long long base = s * kSeg;
-    Bits b[kSegV];
-    load_seg_striped<T, kVec>(w, base, M, lane, b);
-    uint32_t emax = 0, invalid = 0;
-#pragma unroll
-    for (int i = 0; i < kSegV; ++i) {
-      emax = max(emax, seg_top<T>(b[i]));
-      invalid |= Tr::valid_top(b[i]) ^ 1u;
-    }
-    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
-    E = emax > 1u ? emax : 1u;
-    if (__any_sync(0xFFFFFFFFu, invalid)) {
-      // rare: tell a negative zero (valid) from negative, NaN or infinite weights
-      bool bad = false;
-#pragma unroll
-      for (int i = 0; i < kSegV; ++i) bad |= Tr::bad(b[i]);
-      if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) raise_status(status, ST_ENONFINITE);
-    }
-    uint64_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
-    sum = warp_sum_u64(sum);
+    uint64_t sum;
+    seg_sum<T, kVec>(w, base, M, lane, status, sum, E);
     if (lane == 0) {
       const long long rem = M - base;
       SegRec r;
@@ -168,15 +64,6 @@ __global__ void __launch_bounds__(kWThreads, 4) k_w_reduce(const T* __restrict__
 }
 
 // ---- prefix: segment prefixes on the global grid --------------------------
-// A segment sum in grid units: F * 2^(E - Emax + kGridHead), truncated.
-__device__ __forceinline__ u128 grid_value(unsigned long long F, int E, int Emax) {
-  const int sh = E - Emax + kGridHead;
-  uint64_t hi = 0, lo = F;
-  if (sh >= 0) shl128(hi, lo, sh);
-  else shr128(hi, lo, -sh);
-  return u128{lo, hi};
-}
-
 // The per-call constants, written by the thread that owns the last segment:
 // S and the grid exponent, c = S * (1/Z_{N+1}) (integer product; the
 // reciprocal comes from the spacing scan) and, only when W itself is written,

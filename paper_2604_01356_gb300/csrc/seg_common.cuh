@@ -1,0 +1,244 @@
+// Device building blocks shared by the single-instance kernels and the
+// batched persistent kernel, so that both compute bit-identical segment sums,
+// grid prefixes, spacings, keys and in-segment decisions.
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+
+namespace gbr {
+
+// Striped (coalesced) load of one segment: lane holds elements
+//   binary64: 2*lane + 64*i + {0,1},   i < 8
+//   binary32: 4*lane + 128*i + {0..3}, i < 4
+// Missing elements of a ragged last segment read as +0.
+template <typename T, bool kVec>
+__device__ __forceinline__ void load_seg_striped(const T* __restrict__ w, long long base, long long M, int lane,
+                                                 typename FixedTraits<T>::Bits (&b)[kSegV]) {
+  using Bits = typename FixedTraits<T>::Bits;
+  const bool full = base + kSeg <= M;
+  if (sizeof(T) == 8) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long e = base + 2 * lane + 64 * i;
+      if (kVec && full) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(w + e));
+        b[2 * i] = (Bits)v.x;
+        b[2 * i + 1] = (Bits)v.y;
+      } else {
+        b[2 * i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e)) : (Bits)0;
+        b[2 * i + 1] = e + 1 < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e + 1)) : (Bits)0;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const long long e = base + 4 * lane + 128 * i;
+      if (kVec && full) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + e));
+        b[4 * i] = (Bits)v.x;
+        b[4 * i + 1] = (Bits)v.y;
+        b[4 * i + 2] = (Bits)v.z;
+        b[4 * i + 3] = (Bits)v.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          b[4 * i + q] = e + q < M ? (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e + q)) : (Bits)0;
+      }
+    }
+  }
+}
+
+// Lane-major load (lane holds 16 consecutive elements 16*lane + i), used
+// where within-segment order matters (prefixes).
+template <typename T, bool kVec>
+__device__ __forceinline__ void load_seg_blocked(const T* __restrict__ w, long long base, long long M, int lane,
+                                                 typename FixedTraits<T>::Bits (&b)[kSegV]) {
+  using Bits = typename FixedTraits<T>::Bits;
+  const long long e0 = base + (long long)lane * kSegV;
+  const bool full = e0 + kSegV <= M;
+  if (kVec && full) {
+    if (sizeof(T) == 8) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(w + e0 + 2 * i));
+        b[2 * i] = (Bits)v.x;
+        b[2 * i + 1] = (Bits)v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(w + e0 + 4 * i));
+        b[4 * i] = (Bits)v.x;
+        b[4 * i + 1] = (Bits)v.y;
+        b[4 * i + 2] = (Bits)v.z;
+        b[4 * i + 3] = (Bits)v.w;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kSegV; ++i) {
+      const long long e = e0 + i;
+      if (sizeof(T) == 8) b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e)) : (Bits)0;
+      else b[i] = e < M ? (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e)) : (Bits)0;
+    }
+  }
+}
+
+__device__ __forceinline__ void st_xf(unsigned long long* p, const xf& v) {
+  p[0] = v.lo;
+  p[1] = v.hi;
+  p[2] = (unsigned long long)v.e;
+}
+__device__ __forceinline__ xf ld_xf(const unsigned long long* p) { return {p[0], p[1], (long long)p[2]}; }
+
+
+// ---- exact segment sum (Eq. 3 at the segment level) -------------------------
+// One warp, one 512-element segment: the segment exponent E (largest exponent
+// field, at least 1) and the exact sum F of the weights on the grid
+// 2^(E - bias - shift).  Raises ST_ENONFINITE for a negative, NaN or infinite
+// weight.  Every lane returns the same F and E.
+template <typename T>
+__device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits (&b)[kSegV], int lane, int* status,
+                                             uint64_t& F, uint32_t& E) {
+  using Tr = FixedTraits<T>;
+  uint32_t emax = 0, invalid = 0;
+#pragma unroll
+  for (int i = 0; i < kSegV; ++i) {
+    emax = max(emax, seg_top<T>(b[i]));
+    invalid |= Tr::valid_top(b[i]) ^ 1u;
+  }
+  emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+  E = emax > 1u ? emax : 1u;
+  if (__any_sync(0xFFFFFFFFu, invalid)) {
+    // rare: tell a negative zero (valid) from negative, NaN or infinite weights
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < kSegV; ++i) bad |= Tr::bad(b[i]);
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) raise_status(status, ST_ENONFINITE);
+  }
+  uint64_t sum = 0;
+#pragma unroll
+  for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+  F = warp_sum_u64(sum);
+}
+template <typename T, bool kVec>
+__device__ __forceinline__ void seg_sum(const T* __restrict__ w, long long base, long long M, int lane, int* status,
+                                        uint64_t& F, uint32_t& E) {
+  typename FixedTraits<T>::Bits b[kSegV];
+  load_seg_striped<T, kVec>(w, base, M, lane, b);
+  seg_sum_bits<T>(b, lane, status, F, E);
+}
+
+// A segment sum in grid units: F * 2^(E - Emax + kGridHead), truncated.
+__device__ __forceinline__ u128 grid_value(unsigned long long F, int E, int Emax) {
+  const int sh = E - Emax + kGridHead;
+  uint64_t hi = 0, lo = F;
+  if (sh >= 0) shl128(hi, lo, sh);
+  else shr128(hi, lo, -sh);
+  return u128{lo, hi};
+}
+
+// ---- spacings (Algorithm 1) ---------------------------------------------
+constexpr int kZFrac = 88;  // spacing grid 2^-88
+
+// -log v of the draw taken from Philox word x, exactly on the 2^-88 grid:
+// binary32 draws use logf, binary64 draws the binary32-pair table logarithm
+// (tab: the table in shared memory; unused for binary32 draws).
+template <bool F32>
+__device__ __forceinline__ u128 spacing_fixed(uint64_t word, const LogTab* tab) {
+  if (F32) {
+    const float v = __int2float_rn((int)(2u * (uint32_t)(word >> 41) + 1u)) * 0x1p-24f;  // exact
+    return f_to_fixed128<kZFrac>(-logf(v));
+  }
+  const df z = neg_log_draw(2ULL * (word >> 12) + 1ULL, 53, *tab);
+  const u128 f = f_to_fixed128<kZFrac>(z.hi);
+  return (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
+}
+// Philox word k of the stream (seed, instance).
+__device__ __forceinline__ uint64_t philox_word(unsigned long long seed, unsigned long long inst, long long k) {
+  uint64_t words[4];
+  philox4x64_10((uint64_t)(k / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
+  const unsigned q = (unsigned)(k & 3);
+  return q == 0 ? words[0] : q == 1 ? words[1] : q == 2 ? words[2] : words[3];
+}
+// 1 / Z_{N+1}.
+__device__ __forceinline__ xf recip_total(u128 t) { return xf_div(xf_from_u64(1, 0), xf_make(t.hi, t.lo, 0)); }
+
+// ---- map keys and in-segment decisions ---------------------------------------
+__device__ __forceinline__ bool u128_lt(const u128& a, const u128& b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+// key = ceil(Z_i * c) with c = S_grid / Z_{N+1}: U_i * S in grid units,
+// rounded up (so that "prefix >= key" is "W >= U").
+__device__ __forceinline__ u128 map_key(const xf& c, u128 z) {
+  const xf kx = xf_mul_u128(c, z);
+  u128 key = {0ULL, 0ULL};
+  if (!xf_zero(kx)) {
+    uint64_t kh = kx.hi, kl = kx.lo;
+    if (kx.e >= 0) {
+      shl128(kh, kl, kx.e > 1 ? 1 : (int)kx.e);  // key <= S < 2^126: e <= 1
+    } else {
+      const int r = kx.e < -127 ? 128 : (int)(-kx.e);
+      uint64_t th = kh, tl = kl;
+      shr128(th, tl, r);
+      uint64_t bh = th, bl = tl;
+      shl128(bh, bl, r < 128 ? r : 0);
+      const bool frac = r >= 128 ? true : (bh != kh || bl != kl);
+      kh = th;
+      kl = tl + (frac ? 1ULL : 0ULL);
+      if (kl < tl) ++kh;
+    }
+    key = u128{kl, kh};
+  }
+  return key;
+}
+
+// K = ceil(rem / 2^sh) clamped to [1, F]: the segment-grid target of a key
+// that lies rem grid units above the segment's start.
+__device__ __forceinline__ unsigned long long ceil_units(u128 rem, int sh, unsigned long long F) {
+  if (u128_is_zero(rem)) return 1;
+  unsigned long long K;
+  if (sh >= 0) {
+    if (sh >= 128) {
+      K = 1;
+    } else {
+      uint64_t ah = 0, al = 0;  // 2^sh - 1
+      if (sh >= 64) {
+        ah = (sh == 64) ? 0 : ((1ULL << (sh - 64)) - 1);
+        al = ~0ULL;
+      } else {
+        al = (1ULL << sh) - 1;
+      }
+      uint64_t nl = rem.lo + al;
+      uint64_t nh = rem.hi + ah + (nl < rem.lo ? 1ULL : 0ULL);
+      shr128(nh, nl, sh);
+      K = nh ? F : nl;
+    }
+  } else {
+    // rem * 2^-sh; anything at or above 2^63 is past F anyway
+    const int ls = -sh;
+    K = (rem.hi || ls >= 63 || (rem.lo >> (63 - ls))) ? F : (rem.lo << ls);
+  }
+  if (K > F) K = F;
+  if (K < 1) K = 1;
+  return K;
+}
+
+// Exact inclusive prefixes of a segment on its own grid, lane-major (lane l
+// holds elements 16 l .. 16 l + 15): pref[q] = sum of fixed values up to that
+// element.  Non-decreasing across the warp.
+template <typename T>
+__device__ __forceinline__ void seg_prefixes(const typename FixedTraits<T>::Bits (&b)[kSegV], uint32_t E, int lane,
+                                             uint64_t (&pref)[kSegV]) {
+  uint64_t run = 0;
+#pragma unroll
+  for (int q = 0; q < kSegV; ++q) {
+    run += FixedTraits<T>::fixed(b[q], E);
+    pref[q] = run;
+  }
+  const uint64_t off = warp_incl_scan_u64(run, lane) - run;
+#pragma unroll
+  for (int q = 0; q < kSegV; ++q) pref[q] += off;
+}
+
+}  // namespace gbr
