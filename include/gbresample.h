@@ -87,10 +87,12 @@ typedef struct {
   int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 512) */
   int32_t spin_limit;  /* bounded-wait iterations before RS_ETIMEOUT (0 = default) */
   int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of every
-                          look-back scan of the call (spacings, tile prefixes)
+                          look-back scan of the call (spacings, segment prefixes)
                           withholds its publication, so every later tile's bounded
                           wait runs out and RS_ETIMEOUT is latched (results are then
-                          unspecified).  Nothing faults. */
+                          unspecified).  Nothing faults.  Bit 1: rs_resample_w uses
+                          the multi-kernel path instead of the single cooperative
+                          launch (identical results; for comparison). */
   int32_t tile_threads; /* rs_resample_batched: threads per CTA, 128, 256 or 512
                            (0 = the autotuned or default value); ignored elsewhere */
   int32_t reserved;    /* must be zero */

@@ -23,6 +23,7 @@ struct rs_trace_total {
 struct rs_handle {
   int device = 0;
   int* status = nullptr;  // device status word (first device error wins)
+  void* logtab = nullptr; // device copy of the spacing logarithm table (fused path)
   void* ws = nullptr;     // grow-only workspace
   size_t ws_bytes = 0;
   std::string err;
@@ -86,15 +87,26 @@ struct TraceScope {
       p.name = nullptr;
       return;
     }
-    // External records become event nodes when the stream is being captured
-    // into a CUDA graph, and behave as plain records otherwise.
-    cudaEventRecordWithFlags(p.start, st, cudaEventRecordExternal);
+    // While the stream is being captured into a CUDA graph the records must
+    // be external (they become event nodes); otherwise they are plain.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      cs = cudaStreamCaptureStatusNone;
+    }
+    external = cs == cudaStreamCaptureStatusActive;
+    record(p.start);
+  }
+  void record(cudaEvent_t e) {
+    if (external) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
   ~TraceScope() {
     if (!p.name) return;
-    cudaEventRecordWithFlags(p.stop, st, cudaEventRecordExternal);
+    record(p.stop);
     h->pending.push_back(p);
   }
+  bool external = false;
 };
 #define RS_TRACE(h, name, st) TraceScope trace_scope_(h, name, st)
 
@@ -122,7 +134,7 @@ rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec)
     if (o->tile_threads != 0 && o->tile_threads != 128 && o->tile_threads != 256 && o->tile_threads != 512)
       return fail(h, RS_EINVAL, "opts.tile_threads must be 0, 128, 256 or 512");
     r.threads = o->tile_threads;
-    if (o->debug_flags & ~1) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
+    if (o->debug_flags & ~3) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
     r.debug = o->debug_flags;
     r.algo = o->algo;
     r.prec = o->prec;
@@ -171,6 +183,8 @@ struct Plan {
   long long M = 0, nseg = 0, ntile = 0, pblocks = 0;
   int nlev = 0;
   long long lvl_n[kMaxLevels] = {0};
+  int max_blocks = 0;
+  size_t o_agg = 0, o_crel = 0;
   size_t o_wdesc = 0, o_seg = 0, o_emax = 0, o_pre = 0, o_xin = 0, o_xagg = 0, o_lvl[kMaxLevels] = {0}, o_consts = 0;
   // uniforms side
   long long N = 0, ndraw = 0, utiles = 0;
@@ -198,8 +212,13 @@ Plan make_plan(long long M, long long N, bool need_w, bool need_u, bool need_U, 
   p.clear_bytes = L.off;
   if (need_w) {
     p.o_seg = L.take((size_t)p.nseg * sizeof(SegRec));
-    // per-reduce-block exponent maxima, padded to whole 16-byte groups
-    p.o_emax = L.take((size_t)((p.ntile + 3) / 4) * 16);
+    // per-block exponent maxima (reduce blocks, or the fused kernel's CTAs),
+    // padded to whole 16-byte groups; the fused kernel's CTA totals
+    p.max_blocks = num_sms() * 2;
+    const long long ne = p.ntile > p.max_blocks ? p.ntile : p.max_blocks;
+    p.o_emax = L.take((size_t)((ne + 3) / 4) * 16);
+    p.o_agg = L.take((size_t)p.max_blocks * 16);
+    p.o_crel = L.take((size_t)2048 * 16);
     p.o_pre = L.take((size_t)p.nseg * sizeof(SegPre));
     if (need_W) {
       p.o_xin = L.take((size_t)p.nseg * sizeof(SegX));
@@ -371,6 +390,8 @@ rs_status rs_create(rs_handle** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e == cudaSuccess) e = init_log_table();
+  if (e == cudaSuccess) e = cudaMalloc(&h->logtab, log_table_bytes());
+  if (e == cudaSuccess) e = upload_log_table(h->logtab);
   int prio_lo = 0, prio_hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   // the side stream carries short work that the weights pass must not starve
@@ -381,6 +402,7 @@ rs_status rs_create(rs_handle** out) {
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (h->status) cudaFree(h->status);
+    if (h->logtab) cudaFree(h->logtab);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -401,6 +423,7 @@ rs_status rs_destroy(rs_handle* h) {
   cudaError_t e1 = cudaSuccess, e2 = cudaSuccess;
   if (h->ws) e1 = cudaFree(h->ws);
   if (h->status) e2 = cudaFree(h->status);
+  if (h->logtab) cudaFree(h->logtab);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -537,6 +560,42 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   if (N == 0 && !W_out) return RS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(M, N, true, N > 0, false, W_out != nullptr);
+  if (N > 0 && !W_out && !(o.debug & 2)) {
+    // the whole path in one cooperative launch (when the device holds it)
+    if ((s = ensure_ws(h, p.bytes))) return s;
+    if ((s = enqueue_clear(h, p, st))) return s;
+    FusedLaunch F;
+    F.w = w;
+    F.M = M;
+    F.N = N;
+    F.seed = seed;
+    F.inst = instance;
+    F.seg = at<SegRec>(h, p.o_seg);
+    F.emax_g = at<unsigned>(h, p.o_ctr) + 4;
+    F.agg = at<void>(h, p.o_agg);
+    F.rel = at<SegPre>(h, p.o_pre);
+    F.crel = at<void>(h, p.o_crel);
+    F.consts = at<PathConsts>(h, p.o_consts);
+    F.Z = at<void>(h, p.o_Z);
+    F.Ztot = at<void>(h, p.o_Ztot);
+    F.udesc = at<void>(h, p.o_udesc);
+    F.work = at<unsigned>(h, p.o_ctr) + 2;
+    F.bar = at<unsigned>(h, p.o_ctr) + 3;
+    F.status = h->status;
+    F.spin = o.spin;
+    F.withhold_first = o.debug & 1;
+    F.tab = static_cast<const LogTab*>(h->logtab);
+    F.out = out_idx;
+    F.max_blocks = p.max_blocks;
+    cudaError_t e;
+    {
+      RS_TRACE(h, "fused", st);
+      e = launch_fused(f32, aligned(w, 16), F, st);
+    }
+    if (e == cudaSuccess) return RS_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge) return cuda_fail(h, e, "launch_fused");
+    cudaGetLastError();  // the device cannot hold the grid: multi-kernel path
+  }
   if ((s = ensure_ws(h, p.bytes))) return s;
   const bool vec = aligned(w, 16);
   // fork: the workspace clear and the spacing scan (independent of w) run on

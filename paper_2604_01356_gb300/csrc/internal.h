@@ -74,9 +74,13 @@ constexpr int kTileDescBytes = 64;
 int num_sms();
 
 // --- uniforms (Algorithm 1) ---------------------------------------------
-// Draw counts per tile of the spacing scan (256 threads x 1 draw).
-constexpr int kUTile = 256;
+// Draw counts per tile of the spacing scan (256 threads x 4 draws).
+constexpr int kUTile = 1024;
 cudaError_t init_log_table();
+struct LogTab;
+void fill_log_table(LogTab& h);  // host copy of the logarithm table
+size_t log_table_bytes();
+cudaError_t upload_log_table(void* dst);  // synchronous copy into device memory
 struct PathConsts;
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst,
                                 void* Z, void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
@@ -96,6 +100,34 @@ cudaError_t launch_seg_prefix(bool f32, long long M, const SegRec* seg, const in
                               bool withhold_first, cudaStream_t st);
 cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
                            const SegX* xin, const SegX* xagg, const PathConsts* consts, double* W, cudaStream_t st);
+
+// --- fused single-instance path (one cooperative launch) ----------------
+struct LogTab;
+struct FusedLaunch {
+  const void* w;
+  long long M, N;
+  unsigned long long seed, inst;
+  SegRec* seg;
+  unsigned* emax_g;  // cleared
+  void* agg;         // [max_blocks] u128
+  SegPre* rel;       // [nseg]
+  void* crel;        // [2048] u128
+  PathConsts* consts;
+  void* Z;           // [N] u128
+  void* Ztot;
+  void* udesc;       // spacing-scan look-back descriptors (cleared)
+  unsigned* work;    // cleared
+  unsigned* bar;     // cleared
+  int* status;
+  int spin;
+  bool withhold_first;
+  const LogTab* tab;  // device copy of the logarithm table
+  int* out;
+  int max_blocks;
+};
+// Returns cudaErrorCooperativeLaunchTooLarge (nothing launched) when the
+// device cannot hold the whole grid at once.
+cudaError_t launch_fused(bool f32, bool vec, const FusedLaunch& L, cudaStream_t st);
 
 // --- maps (Eq. 2; Algorithms 3, 4, 5) -------------------------------------
 cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,

@@ -22,7 +22,7 @@
 // Comparisons on a given binary64 W are exact: values are compared through
 // their total-order integer keys, which agree with IEEE comparison for every
 // non-NaN value, so all three maps return bit-identical indices.
-#include "seg_common.cuh"
+#include "map_common.cuh"
 
 namespace gbr {
 
@@ -30,138 +30,19 @@ __device__ __forceinline__ long long ldkey(const double* __restrict__ p) {
   return ord_key_bits(__ldg(reinterpret_cast<const long long*>(p)));
 }
 
-// ---------------------------------------------------------------------------
-// Map from weights, over the segment records of the first weights pass.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ u128 seg_pre(const SegPre* __restrict__ pre, long long s) {
-  return u128{__ldcg(&pre[s].lo), __ldcg(&pre[s].hi)};
-}
-__device__ __forceinline__ xf ld_consts_xf(const unsigned long long* p) {
-  return {__ldcg(p), __ldcg(p + 1), (long long)__ldcg(p + 2)};
-}
-
-// Last segment s with P_s < key: a 32-ary search down the index on the
-// monotone 64-bit keys, then an exact fix-up on the 128-bit prefixes only
-// when the keys do not already separate key from its neighbours.
-__device__ __forceinline__ long long fixup_seg(const SegPre* __restrict__ pre, long long n, long long s,
-                                               const u128& key) {
-  int guard = 0;
-  while (s + 1 < n && u128_lt(seg_pre(pre, s + 1), key) && ++guard < 4096) ++s;
-  while (s > 0 && !u128_lt(seg_pre(pre, s), key) && ++guard < 8192) --s;
-  return s;
-}
-__device__ __forceinline__ long long level0_step(const SegPre* __restrict__ pre, const SegIndex& idx, long long c,
-                                                 unsigned long long kb, const u128& key, int lane) {
-  const long long j = c * 32 + lane;
-  const unsigned long long e = j < idx.lvl_n[0] ? __ldcg(idx.lvl[0] + j) : ~0ULL;
-  const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
-  const long long s = c * 32 + (cnt > 0 ? cnt - 1 : 0);
-  const unsigned long long next = __shfl_sync(0xFFFFFFFFu, e, cnt & 31);
-  // key(P_s) < kb < key(P_{s+1}) proves P_s < key <= P_{s+1} (monotone keys)
-  if (cnt > 0 && cnt < 32 && next != kb) return s;
-  return fixup_seg(pre, idx.n, s, key);
-}
-__device__ __forceinline__ long long locate_seg(const SegPre* __restrict__ pre, const SegIndex& idx,
-                                                unsigned long long kb, const u128& key, int lane) {
-  long long c = 0;
-  for (int l = idx.nlev - 1; l >= 1; --l) {
-    const long long j = c * 32 + lane;
-    const unsigned long long e = j < idx.lvl_n[l] ? __ldcg(idx.lvl[l] + j) : ~0ULL;
-    const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
-    c = c * 32 + (cnt > 0 ? cnt - 1 : 0);
-  }
-  return level0_step(pre, idx, c, kb, key, lane);
-}
-// Same with level 1 of the index staged in shared memory.
-__device__ __forceinline__ long long locate_seg_smem(const SegPre* __restrict__ pre, const SegIndex& idx,
-                                                     const unsigned long long* __restrict__ top, int ntop,
-                                                     unsigned long long kb, const u128& key, int lane) {
-  int lo = 0, hi = ntop;  // first entry >= kb
-  while (lo < hi) {
-    const int m = (lo + hi) >> 1;
-    if (top[m] < kb) lo = m + 1;
-    else hi = m;
-  }
-  return level0_step(pre, idx, lo > 0 ? lo - 1 : 0, kb, key, lane);
-}
-
-// Head segment of binary64 weights: number of elements j with
-// sum_{k<=j} w_k < rem (rem = key - P_s as a value).  The weights are put on a
-// 128-bit grid scaled to rem (unit 2^(rem.e + 25), so rem is about 2^100
-// units) and summed with saturation at 2^102: the decision is exact up to 512
-// units, i.e. 2^-91 of rem, whatever the dynamic range of the segment.
-__device__ __forceinline__ u128 sat_add(u128 a, u128 b) {
-  const u128 s = u128_add(a, b);
-  return (s.hi >> 38) ? u128{0ULL, 1ULL << 38} : s;  // cap at 2^102
-}
-__device__ __forceinline__ u128 head_val(uint64_t b, long long ue) {
-  const uint32_t t = (uint32_t)(b >> 52);
-  if (t >= 0x7FFu) return u128{0ULL, 0ULL};
-  const uint64_t m = (b & 0xFFFFFFFFFFFFFULL) | (t ? (1ULL << 52) : 0ULL);
-  const long long sh = (long long)(t > 1u ? t : 1u) - 1075 - ue;
-  if (sh >= 50) return u128{0ULL, m ? (1ULL << 38) : 0ULL};
-  if (sh >= 0) {
-    uint64_t vh = 0, vl = m;
-    shl128(vh, vl, (int)sh);
-    return u128{vl, vh};
-  }
-  return sh > -64 ? u128{m >> (-sh), 0ULL} : u128{0ULL, 0ULL};
-}
-template <bool kVec>
-__device__ __forceinline__ int head_count(const double* __restrict__ w, long long base, long long M, const xf& rem,
-                                          int lane) {
-  using Tr = FixedTraits<double>;
-  if (xf_zero(rem)) return 0;
-  // R = rem / unit = rem.m >> 25, in [2^100, 2^101)
-  uint64_t rh = rem.hi, rl = rem.lo;
-  shr128(rh, rl, 25);
-  const long long ue = rem.e + 25;
-  Tr::Bits b[kSegV];
-  load_seg_blocked<double, kVec>(w, base, M, lane, b);
-  u128 run = {0ULL, 0ULL};
-#pragma unroll
-  for (int i = 0; i < kSegV; ++i) run = sat_add(run, head_val(b[i], ue));
-  u128 incl = run;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const u128 t = shfl_up_v(incl, o);
-    if (lane >= o) incl = sat_add(t, incl);
-  }
-  u128 x = shfl_up_v(incl, 1);
-  if (lane == 0) x = u128{0ULL, 0ULL};
-  int cnt = 0;
-#pragma unroll
-  for (int i = 0; i < kSegV; ++i) {
-    x = sat_add(x, head_val(b[i], ue));
-    cnt += (x.hi < rh || (x.hi == rh && x.lo < rl)) ? 1 : 0;
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-  return cnt;
-}
-template <bool kVec>
-__device__ __forceinline__ int head_count(const float*, long long, long long, const xf&, int) {
-  return 0;  // binary32 weights never need it: their grid is finer than the tolerance
-}
-
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, long long M,
-                                                    const SegRec* __restrict__ seg, const SegPre* __restrict__ pre,
-                                                    SegIndex idx, const PathConsts* __restrict__ consts,
-                                                    const u128* __restrict__ Z, long long N, int G, int ntop,
-                                                    int* __restrict__ out) {
-  using Tr = FixedTraits<T>;
-  using Bits = typename Tr::Bits;
-  extern __shared__ unsigned long long s_top[];  // level 1 of the index when ntop > 0
+__global__ void __launch_bounds__(kMapWarps * 32, 2) k_map_seg(const T* __restrict__ w, long long M,
+                                                              const SegRec* __restrict__ seg,
+                                                              const SegPre* __restrict__ pre, SegIndex idx,
+                                                              const PathConsts* __restrict__ consts,
+                                                              const u128* __restrict__ Z, long long N, int G, int ntop,
+                                                              int* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned long long s_dyn[];
   __shared__ xf s_c;
   __shared__ u128 s_S;
   __shared__ long long s_ge;
   __shared__ int s_Emax;
-  const long long gw0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  // the first sample's spacing sum is fetched while the index is staged
-  u128 z_first = {0ULL, 0ULL};
-  if (gw0 * (long long)G < N) z_first = Z[gw0 * (long long)G];
-  for (int t = threadIdx.x; t < ntop; t += blockDim.x) s_top[t] = __ldcg(idx.lvl[1] + t);
+  for (int t = threadIdx.x; t < ntop; t += blockDim.x) s_dyn[t] = __ldcg(idx.lvl[1] + t);
   if (threadIdx.x == 0) {
     s_c = ld_consts_xf(consts->c);
     s_S = u128{__ldcg(consts->S), __ldcg(consts->S + 1)};
@@ -169,89 +50,36 @@ __global__ void __launch_bounds__(256, 2) k_map_seg(const T* __restrict__ w, lon
     s_Emax = (int)__ldcg((const unsigned long long*)&consts->Emax);
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const long long gw = gw0;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long nseg = idx.n;
-  for (long long g = gw; g * (long long)G < N; g += nw) {
-    const long long i0 = g * (long long)G;
-    const long long i1 = (i0 + G < N) ? i0 + G : N;
-    long long s = -1;  // segment held in registers
-    u128 Ps = {0ULL, 0ULL}, Pn = {0ULL, 0ULL};
-    int sh = 0, len = 0;
-    bool head = false;
-    unsigned long long F = 0;
-    uint64_t pref[kSegV];
-#pragma unroll
-    for (int q = 0; q < kSegV; ++q) pref[q] = 0;
-    for (long long i = i0; i < i1; ++i) {
-      const u128 z = (g == gw0 && i == i0) ? z_first : Z[i];
-      const u128 key = map_key(s_c, z);  // ceil(U_i * S) in grid units
-      if (s < 0 || !(u128_lt(Ps, key) && !u128_lt(Pn, key))) {
-        const unsigned long long kb = u128_key(key);
-        long long ns = -1;
-        if (s >= 0 && u128_lt(Pn, key)) {
-          // forward skip over the next 32 segments (merge walk)
-          const long long j = s + 1 + lane;
-          const unsigned long long e = j < nseg ? __ldcg(idx.lvl[0] + j) : ~0ULL;
-          const int cnt = __popc(__ballot_sync(0xFFFFFFFFu, e < kb));
-          if (cnt < 32) ns = fixup_seg(pre, nseg, s + cnt, key);
-        }
-        if (ns < 0)
-          ns = ntop > 0 ? locate_seg_smem(pre, idx, s_top, ntop, kb, key, lane) : locate_seg(pre, idx, kb, key, lane);
-        s = ns;
-        // the segment's record, prefixes and weights are independent loads
-        Bits b[kSegV];
-        load_seg_blocked<T, kVec>(w, s * kSeg, M, lane, b);
-        const SegRec r = seg[s];
-        Ps = seg_pre(pre, s);
-        Pn = (s + 1 < nseg) ? seg_pre(pre, s + 1) : s_S;
-        sh = r.E - s_Emax + kGridHead;
-        len = r.len;
-        F = r.F;
-        const xf Px = xf_make(Ps.hi, Ps.lo, 0);
-        head = sizeof(T) == 8 && (xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50);
-        if (!head) seg_prefixes<T>(b, (uint32_t)r.E, lane, pref);
-      }
-      const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
-      int cnt;
-      if (head) {
-        cnt = head_count<kVec>(w, s * kSeg, M, xf_make(rem.hi, rem.lo, s_ge), lane);
-      } else {
-        // first element whose exact prefix reaches K = ceil(rem / unit_s)
-        const unsigned long long K = ceil_units(rem, sh, F);
-        cnt = 0;
-#pragma unroll
-        for (int q = 0; q < kSegV; ++q) cnt += pref[q] < K ? 1 : 0;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-      }
-      if (lane == 0) {
-        const long long j = cnt < len ? cnt : len - 1;
-        long long r = s * kSeg + j;
-        if (r > M - 1) r = M - 1;
-        out[i] = (int)r;
-      }
-    }
-  }
+  MapCtx cx;
+  cx.s_top = s_dyn;
+  cx.ntop = ntop;
+  cx.s_pref = s_dyn + ((ntop + 1) & ~1);
+  cx.s_win = reinterpret_cast<u128*>(cx.s_pref + kMapWarps * kSeg);
+  cx.c = s_c;
+  cx.S = s_S;
+  cx.ge = s_ge;
+  cx.Emax = s_Emax;
+  map_groups<T, kVec>(w, M, seg, pre, idx, Z, N, G, cx, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                      ((long long)gridDim.x * blockDim.x) >> 5, out);
 }
-
-constexpr int kMapTopMax = 6144;  // entries (48 KB, the default dynamic shared-memory limit)
 
 template <typename T, bool kVec>
 static cudaError_t map_seg_t(const void* w, long long M, const SegRec* seg, const SegPre* pre, const SegIndex& idx,
                              const PathConsts* consts, const void* Z, long long N, int G, int* out, cudaStream_t st) {
   const long long groups = (N + G - 1) / G;
-  long long blocks = (groups + 7) / 8;
+  long long blocks = (groups + kMapWarps - 1) / kMapWarps;
   const long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   // stage level 1 of the segment index in shared memory when it is small
   int ntop = 0;
   if (idx.nlev >= 2 && idx.lvl_n[1] <= kMapTopMax) ntop = (int)idx.lvl_n[1];
-  const size_t smem = (size_t)ntop * sizeof(unsigned long long);
-  k_map_seg<T, kVec><<<(unsigned)blocks, 256, smem, st>>>((const T*)w, M, seg, pre, idx, consts, (const u128*)Z, N, G,
-                                                          ntop, out);
+  const size_t smem = (size_t)((ntop + 1) & ~1) * sizeof(unsigned long long) +
+                      (size_t)kMapWarps * kSeg * sizeof(unsigned long long) + (size_t)kMapWarps * 32 * sizeof(u128);
+  cudaError_t e = cudaFuncSetAttribute(k_map_seg<T, kVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_map_seg<T, kVec><<<(unsigned)blocks, kMapWarps * 32, smem, st>>>((const T*)w, M, seg, pre, idx, consts,
+                                                                     (const u128*)Z, N, G, ntop, out);
   return cudaGetLastError();
 }
 

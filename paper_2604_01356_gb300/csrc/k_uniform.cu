@@ -2,11 +2,12 @@
 //   z_k = -log(v_k), k = 1..N+1;  Z_i = sum_{k<=i} z_k;  U_i = Z_i / Z_{N+1}.
 // (The printed normaliser Z_{i+1} is read as Z_{N+1}.)
 //
-// GB300 form.  One pass over the N+1 draws: each thread takes one draw,
-// evaluates the spacing (binary32-pair log for binary64 draws, binary32 logf
-// for binary32 draws), converts it EXACTLY to an integer on a 2^-88 grid and
-// the block scans them as unsigned 128-bit integers; tiles of 256 draws chain
-// their sums by decoupled look-back.  Integer sums make Z
+// GB300 form.  One pass over the N+1 draws: each thread takes four
+// consecutive draws (the four words of one Philox block), evaluates the
+// spacings (binary32-pair log for binary64 draws, binary32 logf for binary32
+// draws), converts them EXACTLY to integers on a 2^-88 grid and the block
+// scans them as unsigned 128-bit integers; tiles of 1024 draws chain their
+// sums by decoupled look-back.  Integer sums make Z
 // exact, monotone and independent of scheduling.  The resampling map consumes
 // Z directly; when U itself is wanted a second kernel rounds Z_i / Z_{N+1}
 // to binary64 (monotone in Z_i by construction).
@@ -18,21 +19,6 @@ namespace gbr {
 
 __device__ LogTab g_logtab;
 
-constexpr int kUThreads = 256;
-constexpr int kUWarps = kUThreads / kWarp;
-constexpr int kUItems = 1;  // one draw per thread (short dependent chains)
-static_assert(kUThreads * kUItems == kUTile, "uniform tile");
-
-// 1/Z_{N+1} as an xf, once per call by the thread that produced Z_{N+1}
-// (binary64-pair division, out of line; this kernel runs beside the weights
-// pass, so the cost is off the critical path).
-__device__ __noinline__ void store_recip(unsigned long long* dst, u128 t) {
-  const xf r = recip_total(t);
-  dst[0] = r.lo;
-  dst[1] = r.hi;
-  dst[2] = (unsigned long long)r.e;
-}
-
 template <bool F32>
 __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, unsigned long long seed,
                                                            unsigned long long inst, u128* __restrict__ Z,
@@ -40,8 +26,7 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
                                                            TileDesc<u128>* desc, unsigned* ctr, int* status,
                                                            int spin_limit, bool withhold_first) {
   __shared__ LogTab tab;
-  __shared__ u128 s_wsum[kUWarps];
-  __shared__ u128 s_woff[kUWarps];
+  __shared__ UniformTileSmem us;
   __shared__ unsigned s_tile;
   if (!F32) {
     for (int i = threadIdx.x; i < 129; i += kUThreads) {
@@ -51,53 +36,7 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
   }
   if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
   __syncthreads();
-  const long long tile = s_tile;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long k0 = tile * kUTile + (long long)threadIdx.x * kUItems;
-
-  u128 pre[kUItems];  // thread-local inclusive prefixes
-  u128 run = {0ULL, 0ULL};
-  // each thread evaluates the Philox block of its own draw (four neighbouring
-  // threads share a block; recomputing it is cheaper than the shuffles' wait)
-  const uint64_t word = philox_word(seed, inst, k0);
-#pragma unroll
-  for (int q = 0; q < kUItems; ++q) {
-    const long long k = k0 + q;
-    const u128 f = k < ndraw ? spacing_fixed<F32>(word, &tab) : u128{0ULL, 0ULL};
-    run = u128_add(run, f);
-    pre[q] = run;
-  }
-  const u128 incl = warp_incl_scan_v(run, lane);
-  const u128 lane_off = u128_sub(incl, run);
-  if (lane == 31) s_wsum[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    const u128 v = lane < kUWarps ? s_wsum[lane] : u128{0ULL, 0ULL};
-    const u128 wi = warp_incl_scan_v(v, lane);
-    const u128 agg = shfl_v(wi, kUWarps - 1);
-    u128 excl = {0ULL, 0ULL};
-    if (tile == 0) {
-      if (lane == 0 && !withhold_first) lb_publish(desc, 0, agg, true);
-    } else {
-      if (lane == 0) lb_publish(desc, tile, agg, false);
-      excl = lb_exclusive(desc, tile, lane, spin_limit, status);
-      if (lane == 0) lb_publish_inc(desc, tile, u128_add(excl, agg));
-    }
-    if (lane < kUWarps) s_woff[lane] = u128_add(excl, u128_sub(wi, v));
-  }
-  __syncthreads();
-  const u128 off = u128_add(s_woff[warp], lane_off);
-#pragma unroll
-  for (int q = 0; q < kUItems; ++q) {
-    const long long k = k0 + q;
-    if (k < ndraw - 1) {
-      Z[k] = u128_add(off, pre[q]);
-    } else if (k == ndraw - 1) {
-      const u128 t = u128_add(off, pre[q]);
-      *Ztot = t;
-      store_recip(consts->invZ, t);
-    }
-  }
+  uniform_tile<F32>(s_tile, ndraw, seed, inst, Z, Ztot, consts, desc, status, spin_limit, withhold_first, &tab, us);
 }
 
 // U_i = Z_i / Z_{N+1} rounded to binary64: integer multiply by the reciprocal
@@ -126,8 +65,7 @@ __global__ void k_philox_words(unsigned long long seed, unsigned long long inst,
   }
 }
 
-cudaError_t init_log_table() {
-  LogTab h;
+void fill_log_table(LogTab& h) {
   for (int k = 0; k <= 128; ++k) {
     const double c = 1.0 - k / 256.0;
     const double nl = -std::log(c);
@@ -136,7 +74,20 @@ cudaError_t init_log_table() {
     h.nlogc[k] = make_float2(nh, (float)(nl - (double)nh));
     h.invc[k] = make_float2(ih, (float)(ic - (double)ih));
   }
+}
+
+cudaError_t init_log_table() {
+  LogTab h;
+  fill_log_table(h);
   return cudaMemcpyToSymbol(g_logtab, &h, sizeof(h));
+}
+
+size_t log_table_bytes() { return sizeof(LogTab); }
+
+cudaError_t upload_log_table(void* dst) {
+  LogTab h;
+  fill_log_table(h);
+  return cudaMemcpy(dst, &h, sizeof(h), cudaMemcpyHostToDevice);
 }
 
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,

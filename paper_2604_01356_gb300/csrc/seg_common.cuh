@@ -97,28 +97,59 @@ __device__ __forceinline__ xf ld_xf(const unsigned long long* p) { return {p[0],
 // field, at least 1) and the exact sum F of the weights on the grid
 // 2^(E - bias - shift).  Raises ST_ENONFINITE for a negative, NaN or infinite
 // weight.  Every lane returns the same F and E.
+// Fixed-point value of a valid (non-negative, finite) binary64 on the grid
+// 2^(E - 1075), in 32-bit operations: FixedTraits<double>::fixed restricted
+// to valid inputs (m >> d is 0 for d >= 53).
+__device__ __forceinline__ uint64_t fixed64_valid(uint64_t b, uint32_t E) {
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t t = hi >> 20;  // exponent field (the sign is 0)
+  const uint32_t mh = (hi & 0xFFFFFu) | (t ? 0x100000u : 0u);
+  const uint32_t d = E - (t ? t : 1u);
+  // (mh:lo) >> d in two clamped funnel shifts
+  const uint32_t d1 = min(d, 32u);
+  const uint32_t xlo = __funnelshift_rc(lo, mh, d1);
+  const uint32_t xhi = __funnelshift_rc(mh, 0u, d1);
+  const uint32_t rlo = __funnelshift_rc(xlo, xhi, d - d1);
+  return ((uint64_t)xhi << 32) | rlo;
+}
+
 template <typename T>
 __device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits (&b)[kSegV], int lane, int* status,
                                              uint64_t& F, uint32_t& E) {
   using Tr = FixedTraits<T>;
-  uint32_t emax = 0, invalid = 0;
+  // the largest sign+exponent field: below the all-ones exponent only when
+  // every element is a non-negative finite number
+  uint32_t tmax = 0;
 #pragma unroll
-  for (int i = 0; i < kSegV; ++i) {
-    emax = max(emax, seg_top<T>(b[i]));
-    invalid |= Tr::valid_top(b[i]) ^ 1u;
-  }
-  emax = __reduce_max_sync(0xFFFFFFFFu, emax);
-  E = emax > 1u ? emax : 1u;
-  if (__any_sync(0xFFFFFFFFu, invalid)) {
-    // rare: tell a negative zero (valid) from negative, NaN or infinite weights
+  for (int i = 0; i < kSegV; ++i) tmax = max(tmax, Tr::top(b[i]));
+  tmax = __reduce_max_sync(0xFFFFFFFFu, tmax);
+  constexpr uint32_t kTopInf = sizeof(T) == 8 ? 0x7FFu : 0xFFu;
+  uint64_t sum = 0;
+  if (tmax < kTopInf) {
+    E = tmax > 1u ? tmax : 1u;
+    if (sizeof(T) == 8) {
+#pragma unroll
+      for (int i = 0; i < kSegV; ++i) sum += fixed64_valid((uint64_t)b[i], E);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+    }
+  } else {
+    // rare: negative zeros (valid), or negative, NaN or infinite weights,
+    // which add nothing and are reported
+    uint32_t emax = 0;
     bool bad = false;
 #pragma unroll
-    for (int i = 0; i < kSegV; ++i) bad |= Tr::bad(b[i]);
+    for (int i = 0; i < kSegV; ++i) {
+      emax = max(emax, seg_top<T>(b[i]));
+      bad |= Tr::bad(b[i]);
+    }
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    E = emax > 1u ? emax : 1u;
     if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) raise_status(status, ST_ENONFINITE);
-  }
-  uint64_t sum = 0;
 #pragma unroll
-  for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+    for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+  }
   F = warp_sum_u64(sum);
 }
 template <typename T, bool kVec>
@@ -163,6 +194,82 @@ __device__ __forceinline__ uint64_t philox_word(unsigned long long seed, unsigne
 }
 // 1 / Z_{N+1}.
 __device__ __forceinline__ xf recip_total(u128 t) { return xf_div(xf_from_u64(1, 0), xf_make(t.hi, t.lo, 0)); }
+
+// ---- one tile of the spacing scan ------------------------------------------
+// 256 threads x 4 draws (one Philox block per thread): spacings on the 2^-88
+// grid, exact 128-bit block scan, tiles chained by decoupled look-back on the
+// tile index (tiles are numbered in the order they start, so a tile only
+// waits on tiles that are already running).  Writes Z_1..Z_N, Z_{N+1} and
+// 1/Z_{N+1}.  tab: the logarithm table in shared memory (binary64 draws).
+constexpr int kUThreads = 256;
+constexpr int kUWarps = kUThreads / kWarp;
+constexpr int kUItems = 4;
+static_assert(kUThreads * kUItems == kUTile, "uniform tile");
+
+struct UniformTileSmem {
+  u128 wsum[kUWarps];
+  u128 woff[kUWarps];
+};
+
+// 1/Z_{N+1} as an xf, once per call by the thread that produced Z_{N+1}
+// (out of line: binary64-pair division).
+static __device__ __noinline__ void store_recip(unsigned long long* dst, u128 t) {
+  const xf r = recip_total(t);
+  dst[0] = r.lo;
+  dst[1] = r.hi;
+  dst[2] = (unsigned long long)r.e;
+}
+
+template <bool F32>
+__device__ __forceinline__ void uniform_tile(long long tile, long long ndraw, unsigned long long seed,
+                                             unsigned long long inst, u128* __restrict__ Z, u128* __restrict__ Ztot,
+                                             PathConsts* consts, TileDesc<u128>* desc, int* status, int spin_limit,
+                                             bool withhold_first, const LogTab* tab, UniformTileSmem& us) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long k0 = tile * kUTile + (long long)threadIdx.x * kUItems;
+  // the thread's four draws are the four words of one Philox block
+  uint64_t words[4];
+  philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
+  u128 pre[kUItems];  // thread-local inclusive prefixes
+  u128 run = {0ULL, 0ULL};
+#pragma unroll
+  for (int q = 0; q < kUItems; ++q) {
+    const u128 f = k0 + q < ndraw ? spacing_fixed<F32>(words[q], tab) : u128{0ULL, 0ULL};
+    run = u128_add(run, f);
+    pre[q] = run;
+  }
+  const u128 incl = warp_incl_scan_v(run, lane);
+  const u128 lane_off = u128_sub(incl, run);
+  if (lane == 31) us.wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const u128 v = lane < kUWarps ? us.wsum[lane] : u128{0ULL, 0ULL};
+    const u128 wi = warp_incl_scan_v(v, lane);
+    const u128 agg = shfl_v(wi, kUWarps - 1);
+    u128 excl = {0ULL, 0ULL};
+    if (tile == 0) {
+      if (lane == 0 && !withhold_first) lb_publish(desc, 0, agg, true);
+    } else {
+      if (lane == 0) lb_publish(desc, tile, agg, false);
+      excl = lb_exclusive(desc, tile, lane, spin_limit, status);
+      if (lane == 0) lb_publish_inc(desc, tile, u128_add(excl, agg));
+    }
+    if (lane < kUWarps) us.woff[lane] = u128_add(excl, u128_sub(wi, v));
+  }
+  __syncthreads();
+  const u128 off = u128_add(us.woff[warp], lane_off);
+#pragma unroll
+  for (int q = 0; q < kUItems; ++q) {
+    const long long k = k0 + q;
+    if (k < ndraw - 1) {
+      Z[k] = u128_add(off, pre[q]);
+    } else if (k == ndraw - 1) {
+      const u128 t = u128_add(off, pre[q]);
+      *Ztot = t;
+      store_recip(consts->invZ, t);
+    }
+  }
+}
 
 // ---- map keys and in-segment decisions ---------------------------------------
 __device__ __forceinline__ bool u128_lt(const u128& a, const u128& b) {

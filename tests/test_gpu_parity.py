@@ -288,3 +288,69 @@ def test_host_argument_errors(g, h):
         g.rs_resample_w(h.h, None, 8, 4, 1, 0, out)
     g.rs_resample_w(h.h, w, 8, 0, 1, 0, None)  # N = 0 is a no-op
     assert h.status() == g.RS_OK
+
+
+# -------------------------------------------------------------- tracing ----
+def test_tracing_outside_capture_reports_kernels(g, h):
+    w = workloads.weights_lognormal(100_000, 2.0, seed=4)
+    out = torch.empty(500, dtype=torch.int32, device="cuda")
+    wd = dev(w)
+    g.rs_trace_enable(h.h, True)
+    try:
+        for _ in range(3):
+            g.rs_resample_w(h.h, wd, w.size, 500, 1, 0, out)  # one cooperative launch
+            g.rs_resample_w(h.h, wd, w.size, 500, 1, 0, out, None, g.opts(debug_flags=2))  # multi-kernel
+        g.rs_trace_collect(h.h)
+        rep = g.rs_trace_report(h.h)
+    finally:
+        g.rs_trace_enable(h.h, False)
+        g.rs_trace_reset(h.h)
+    assert h.status() == g.RS_OK
+    for name in ("fused", "w_reduce", "seg_prefix", "uniform_scan", "map_seg"):
+        n, ms = rep[name]
+        assert n == 3 and ms > 0.0, (name, rep[name])
+
+
+# ------------------------------------ fused launch vs multi-kernel path ----
+FUSED_CASES = [(1, 1), (2, 5), (513, 1000), (9 * 4096 + 5, 4097), (300_000, 64), (1_000_003, 300_001)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("M,N", FUSED_CASES)
+def test_fused_equals_multikernel(g, h, prec, M, N):
+    w = workloads.weights_lognormal(M, 2.0, seed=M)
+    p = g.RS_F64 if prec == "f64" else g.RS_F32_COMP
+    if prec == "f32":
+        w = w.astype(np.float32)
+    wd = dev(w)
+    a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    b = torch.full((N,), -2, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, N, 9, 2, a, None, g.opts(prec=p))
+    g.rs_resample_w(h.h, wd, M, N, 9, 2, b, None, g.opts(prec=p, debug_flags=2))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(host(a), host(b))
+
+
+@pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
+def test_fused_equals_multikernel_adversarial(g, h, kind):
+    M, N = 7 * 4096 + 3, 5000
+    w = workloads.adversarial_weights(kind, M, seed=4)
+    wd = dev(w)
+    a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    b = torch.full((N,), -2, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, N, 5, 0, a)
+    g.rs_resample_w(h.h, wd, M, N, 5, 0, b, None, g.opts(debug_flags=2))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(host(a), host(b))
+
+
+def test_fused_bounded_wait_times_out_and_context_survives(g, h):
+    w = workloads.weights_lognormal(50_000, 2.0, seed=3)
+    wd = dev(w)
+    out = torch.empty(5000, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, w.size, 5000, 1, 0, out, None, g.opts(spin_limit=200, debug_flags=1))
+    assert h.status() == g.RS_ETIMEOUT
+    g.rs_resample_w(h.h, wd, w.size, 5000, 1, 0, out)
+    assert h.status() == g.RS_OK
+    r = host(out)
+    assert r.min() >= 0 and r.max() < w.size
