@@ -224,30 +224,19 @@ __device__ __forceinline__ void seg_cache_resolve(SegCache& c, const T* __restri
   const bool mine = (grp >> lane) & 1u;
   const u128 rem = (mine && u128_lt(c.Ps, key)) ? u128_sub(key, c.Ps) : u128{0ULL, 0ULL};
   int cnt = 0;
-  // In a head segment a key less than 2^50 segment units past its start
-  // needs exact per-element sums; any other key is decided by the
+  // In a head segment a key less than 2^50 segment units past its start may
+  // need exact per-element sums; any other key is decided by the
   // segment-grid prefixes to 2^-41 relative.
-  bool exact = false;
+  bool small = false;
   if (c.head && mine) {
     const xf rx = xf_make(rem.hi, rem.lo, 0);
-    exact = xf_zero(rx) || rx.e + kXfTop < (long long)c.sh + 50;
+    small = xf_zero(rx) || rx.e + kXfTop < (long long)c.sh + 50;
   }
-  const unsigned gx = __ballot_sync(0xFFFFFFFFu, exact);
-  const unsigned gn = grp & ~gx;
+  // first element whose exact prefix reaches K = ceil(rem / unit_s)
+  const unsigned long long K = ceil_units(rem, c.sh, c.F);
+  const unsigned gn = grp;
   {
-    unsigned gg = gx;
-    while (gg) {
-      const int jl = __ffs(gg) - 1;
-      gg &= gg - 1;
-      const u128 rj = shfl_v(rem, jl);
-      const int cj = head_count<kVec>(w, sc * kSeg, M, xf_make(rj.hi, rj.lo, ge), lane);
-      if (lane == jl) cnt = cj;
-    }
-  }
-  if (gn) {
-    // first element whose exact prefix reaches K = ceil(rem / unit_s)
     const bool mn = (gn >> lane) & 1u;
-    const unsigned long long K = ceil_units(rem, c.sh, c.F);
     if (__popc(gn) <= kLeafCount) {
       unsigned gg = gn;
       while (gg) {
@@ -278,6 +267,40 @@ __device__ __forceinline__ void seg_cache_resolve(SegCache& c, const T* __restri
         }
         cnt = lo;
       }
+    }
+  }
+  if (__any_sync(0xFFFFFFFFu, small)) {
+    // Every element is truncated by less than one unit on the segment grid,
+    // so its exact prefix lies in [pref, pref + len): the grid count is the
+    // exact count unless some grid prefix lies in [K - len, K), or K was
+    // clamped at the segment total.  Only such keys take the exact sums.
+    const long long len = c.len;
+    bool amb = false;
+    if (small) {
+      if (K >= c.F) amb = true;
+      else if ((long long)K <= len) amb = cnt > 0;
+    }
+    unsigned chk = __ballot_sync(0xFFFFFFFFu, small && K < c.F && (long long)K > len);
+    int cnt2 = -1;
+    while (chk) {
+      const int jl = __ffs(chk) - 1;
+      chk &= chk - 1;
+      const unsigned long long K2 = __shfl_sync(0xFFFFFFFFu, K, jl) - (unsigned long long)len;
+      int cj = 0;
+#pragma unroll
+      for (int q = 0; q < kSegV; ++q) cj += c.pref[q] < K2 ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) cj += __shfl_xor_sync(0xFFFFFFFFu, cj, o);
+      if (lane == jl) cnt2 = cj;
+    }
+    if (cnt2 >= 0) amb = cnt2 != cnt;
+    unsigned gx = __ballot_sync(0xFFFFFFFFu, small && amb);
+    while (gx) {
+      const int jl = __ffs(gx) - 1;
+      gx &= gx - 1;
+      const u128 rj = shfl_v(rem, jl);
+      const int cj = head_count<kVec>(w, sc * kSeg, M, xf_make(rj.hi, rj.lo, ge), lane);
+      if (lane == jl) cnt = cj;
     }
   }
   if (mine) {

@@ -1,0 +1,159 @@
+"""GPU parity at the full workload sizes the benchmark measures.
+
+Every index of every full-size instance is compared with the oracle (which
+finishes these sizes in about a second each): boundary-only differences end
+to end, bit-exact for the maps given the oracle's own W and U.  The engmf
+instance runs exactly as the benchmark times it: one rs_resample_w call
+captured in a CUDA graph and replayed.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity_util import ABS_F32, REL_F64, assert_boundary_only
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2604_01356_gb300 as g
+    return g
+
+
+@pytest.fixture(scope="module")
+def h(g):
+    hd = g.Handle()
+    yield hd
+    hd.close()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def engmf():
+    wl = workloads.make("engmf")
+    return wl, oracle.resample(wl.w, wl.N, wl.seed)
+
+
+def test_engmf_graph_replay_full(g, h, engmf):
+    """M = 16,777,216 binary64 weights, N = 4,096: the benchmark's launch
+    (warm-up call, capture, replays), every index checked."""
+    wl, (r_ref, W_ref, U_ref) = engmf
+    wd = torch.from_numpy(wl.w).cuda()
+    out = torch.full((wl.N,), -1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out, None, None, stream=stream)
+    stream.synchronize()
+    assert h.status() == g.RS_OK
+    first = host(out).copy()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out, None, None, stream=torch.cuda.current_stream())
+    out.fill_(-1)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert h.status() == g.RS_OK
+    r = host(out)
+    assert np.array_equal(r, first)  # replays give the direct call's result
+    n = assert_boundary_only(r, r_ref, W_ref, U_ref, rel=REL_F64)
+    assert n == 0  # no sample of this instance sits within 1e-12 of a boundary
+
+
+@pytest.mark.parametrize("algo", ["dac", "binary", "linear"])
+def test_engmf_maps_bit_exact_full(g, h, engmf, algo):
+    """The paper's map-only protocol at full size: the three maps on the
+    oracle's W and U are bit-exact to its brute-force inverse CDF."""
+    wl, (r_ref, W_ref, U_ref) = engmf
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    a = {"dac": g.RS_MAP_DAC, "binary": g.RS_MAP_BINARY, "linear": g.RS_MAP_LINEAR}[algo]
+    g.rs_map(h.h, torch.from_numpy(W_ref).cuda(), wl.M, torch.from_numpy(U_ref).cuda(), wl.N, out, g.opts(algo=a))
+    assert np.array_equal(host(out), r_ref)
+
+
+def test_small_full(g, h):
+    """M = 4,096 Exp(1) weights, N = 1,024 (the paper's regime M/N = 4)."""
+    wl = workloads.make("small")
+    r_ref, W_ref, U_ref = oracle.resample(wl.w, wl.N, wl.seed)
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, torch.from_numpy(wl.w).cuda(), wl.M, wl.N, wl.seed, 0, out)
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, rel=REL_F64)
+
+
+def test_bootstrap_full(g, h):
+    """M = N = 4,194,304 bootstrap-filter weights (highly degenerate)."""
+    wl = workloads.make("bootstrap")
+    r_ref, W_ref, U_ref = oracle.resample(wl.w, wl.N, wl.seed)
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, torch.from_numpy(wl.w).cuda(), wl.M, wl.N, wl.seed, 0, out)
+    assert h.status() == g.RS_OK
+    r = host(out)
+    assert_boundary_only(r, r_ref, W_ref, U_ref, rel=REL_F64)
+    assert np.all(wl.w[r] > 0)
+
+
+@pytest.fixture(scope="module")
+def stress():
+    return workloads.make("stress")
+
+
+def test_stress_f64_full(g, h, stress):
+    """M = 67,108,864 weights of total 1e-9 beside a spike of mass 1 - 1e-9,
+    N = 65,536, binary64."""
+    wl = stress
+    r_ref, W_ref, U_ref = oracle.resample(wl.w, wl.N, wl.seed)
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, torch.from_numpy(wl.w).cuda(), wl.M, wl.N, wl.seed, 0, out)
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, rel=REL_F64)
+
+
+def test_stress_f32_comp_full(g, h, stress):
+    """The same instance in binary32 with compensated sums: indices within
+    4 * 2^-23 of a boundary of the oracle's binary32-weight W may differ, and
+    the cumulative weights stay within that bound of the binary64 ones."""
+    wl = stress
+    r_ref, W_ref, U_ref = oracle.resample(wl.w32, wl.N, wl.seed, single=True)
+    wd = torch.from_numpy(wl.w32).cuda()
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out, None, g.opts(prec=g.RS_F32_COMP))
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+    W32 = torch.empty(wl.M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, wd, wl.M, W32, g.opts(prec=g.RS_F32_COMP))
+    W64_ref, _ = oracle.cumulative(wl.w)
+    assert np.max(np.abs(host(W32) - W64_ref)) <= ABS_F32
+
+
+def test_batched_full(g, h):
+    """8,192 EnGMF-shaped binary32 instances in one persistent launch: every
+    index of every instance against the oracle's per-instance path."""
+    wl = workloads.make("batched")
+    K = wl.info["K"]
+    r_ref = oracle.resample_batched(wl.w, wl.woff, wl.roff, wl.seed, single=True)
+    out = torch.full((int(wl.roff[-1]),), -1, dtype=torch.int32, device="cuda")
+    g.rs_resample_batched(h.h, torch.from_numpy(wl.w).cuda(), torch.from_numpy(wl.woff).cuda(),
+                          torch.from_numpy(wl.roff).cuda(), K, wl.seed, out, wl.woff, wl.roff)
+    assert h.status() == g.RS_OK
+    r = host(out)
+    mism = np.nonzero(r != r_ref)[0]
+    # a mismatch must sit on a boundary of its own instance's binary32-weight W
+    assert mism.size <= 1e-4 * r.size, mism.size
+    for i in mism[:200]:
+        k = int(np.searchsorted(wl.roff, i, side="right") - 1)
+        a, b = int(wl.woff[k]), int(wl.woff[k + 1])
+        rr, W, U = oracle.resample(wl.w[a:b], int(wl.roff[k + 1] - wl.roff[k]), wl.seed, instance=k, single=True)
+        j = i - int(wl.roff[k])
+        assert rr[j] == r_ref[i]
+        lo, hi = sorted((int(r[i]), int(rr[j])))
+        assert np.all(np.abs(U[j] - W[lo:hi]) <= ABS_F32)
