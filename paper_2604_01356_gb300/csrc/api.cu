@@ -24,6 +24,7 @@ struct rs_handle {
   int device = 0;
   int* status = nullptr;  // device status word (first device error wins)
   void* logtab = nullptr; // device copy of the spacing logarithm table (fused path)
+  unsigned* xch = nullptr; // exchange area of the fused kernel (epoch + slots)
   void* ws = nullptr;     // grow-only workspace
   size_t ws_bytes = 0;
   std::string err;
@@ -392,6 +393,8 @@ rs_status rs_create(rs_handle** out) {
   if (e == cudaSuccess) e = init_log_table();
   if (e == cudaSuccess) e = cudaMalloc(&h->logtab, log_table_bytes());
   if (e == cudaSuccess) e = upload_log_table(h->logtab);
+  if (e == cudaSuccess) e = cudaMalloc(&h->xch, kFusedXchBytes);
+  if (e == cudaSuccess) e = cudaMemset(h->xch, 0, kFusedXchBytes);
   int prio_lo = 0, prio_hi = 0;
   if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   // the side stream carries short work that the weights pass must not starve
@@ -403,6 +406,7 @@ rs_status rs_create(rs_handle** out) {
     cudaGetLastError();
     if (h->status) cudaFree(h->status);
     if (h->logtab) cudaFree(h->logtab);
+    if (h->xch) cudaFree(h->xch);
     if (h->side) cudaStreamDestroy(h->side);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -424,6 +428,7 @@ rs_status rs_destroy(rs_handle* h) {
   if (h->ws) e1 = cudaFree(h->ws);
   if (h->status) e2 = cudaFree(h->status);
   if (h->logtab) cudaFree(h->logtab);
+  if (h->xch) cudaFree(h->xch);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
@@ -561,9 +566,9 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(M, N, true, N > 0, false, W_out != nullptr);
   if (N > 0 && !W_out && !(o.debug & 2)) {
-    // the whole path in one cooperative launch (when the device holds it)
+    // the whole path in one cooperative launch (when the device holds it);
+    // it needs no cleared workspace
     if ((s = ensure_ws(h, p.bytes))) return s;
-    if ((s = enqueue_clear(h, p, st))) return s;
     FusedLaunch F;
     F.w = w;
     F.M = M;
@@ -571,22 +576,15 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
     F.seed = seed;
     F.inst = instance;
     F.seg = at<SegRec>(h, p.o_seg);
-    F.emax_g = at<unsigned>(h, p.o_ctr) + 4;
-    F.agg = at<void>(h, p.o_agg);
     F.rel = at<SegPre>(h, p.o_pre);
     F.crel = at<void>(h, p.o_crel);
-    F.consts = at<PathConsts>(h, p.o_consts);
     F.Z = at<void>(h, p.o_Z);
-    F.Ztot = at<void>(h, p.o_Ztot);
-    F.udesc = at<void>(h, p.o_udesc);
-    F.work = at<unsigned>(h, p.o_ctr) + 2;
-    F.bar = at<unsigned>(h, p.o_ctr) + 3;
+    F.xch = h->xch;
     F.status = h->status;
     F.spin = o.spin;
     F.withhold_first = o.debug & 1;
     F.tab = static_cast<const LogTab*>(h->logtab);
     F.out = out_idx;
-    F.max_blocks = p.max_blocks;
     cudaError_t e;
     {
       RS_TRACE(h, "fused", st);

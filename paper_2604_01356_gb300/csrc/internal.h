@@ -102,28 +102,25 @@ cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const
                            const SegX* xin, const SegX* xagg, const PathConsts* consts, double* W, cudaStream_t st);
 
 // --- fused single-instance path (one cooperative launch) ----------------
+// Exchange area of the fused kernel (owned by the handle, zeroed once): an
+// epoch word, then two slots of 32 bytes per CTA.
+constexpr int kFusedMaxCtas = 256;
+constexpr int kFusedXchBytes = 256 + 2 * kFusedMaxCtas * 32;
 struct LogTab;
 struct FusedLaunch {
   const void* w;
   long long M, N;
   unsigned long long seed, inst;
-  SegRec* seg;
-  unsigned* emax_g;  // cleared
-  void* agg;         // [max_blocks] u128
+  SegRec* seg;       // [nseg]
   SegPre* rel;       // [nseg]
-  void* crel;        // [2048] u128
-  PathConsts* consts;
+  void* crel;        // [1024] u128
   void* Z;           // [N] u128
-  void* Ztot;
-  void* udesc;       // spacing-scan look-back descriptors (cleared)
-  unsigned* work;    // cleared
-  unsigned* bar;     // cleared
+  unsigned* xch;     // kFusedXchBytes, zeroed when allocated
   int* status;
   int spin;
   bool withhold_first;
   const LogTab* tab;  // device copy of the logarithm table
   int* out;
-  int max_blocks;
 };
 // Returns cudaErrorCooperativeLaunchTooLarge (nothing launched) when the
 // device cannot hold the whole grid at once.

@@ -1,443 +1,828 @@
 // The whole single-instance path of rs_resample_w (Eq. 3, Algorithm 1 and
-// the segmented map of Eq. 2) in ONE cooperative launch: every CTA is
-// resident, and the phases are separated by grid-wide barriers instead of
-// kernel boundaries.
+// the segmented map of Eq. 2) in ONE cooperative launch, one CTA per SM.
 //
-//   phase 1  the spacing-scan tiles (Algorithm 1, tiles chained by decoupled
-//            look-back, assigned by CTA index), then exact segment sums (one
-//            warp per 512 weights): a static share per warp, the rest from a
-//            shared queue so that the CTAs that drew spacing tiles take less.
-//   barrier
-//   phase 2  every CTA owns a contiguous range of segments: grid values on
-//            the global grid (needs the largest exponent, known only now),
-//            summed exactly; the CTA total is published.
-//   barrier
-//   phase 3  every CTA scans all CTA totals (the CTA-level prefixes and S)
-//            and computes S / Z_{N+1}; then the map: a sample finds its CTA
-//            range by binary search over those prefixes, its segment by an
-//            exact scan of that range's segment sums (32 at a time, staged
-//            in shared memory), and its element as in the standalone map.
-//            No global segment prefixes or search index are written.
+// Every CTA owns a contiguous, balanced range of the 512-weight segments and
+// a contiguous range of the N+1 draws (and of the N samples):
 //
-// Every barrier wait is bounded by spin_limit polls, after which the CTA
-// latches RS_ETIMEOUT and continues (results are then unspecified, nothing
-// hangs).  Arithmetic is that of the multi-kernel path, so the indices are
-// identical to it.
+//   phase 1  the CTA's draws: Philox, spacings -log v on the 2^-88 grid and
+//            their exact in-CTA inclusive prefixes (Algorithm 1);
+//            the CTA's segments: streamed into shared memory by bulk async
+//            copies (TMA engine, a ring of stages completed on mbarriers),
+//            exact segment sums (one warp per segment).
+//   exchange 1  every CTA publishes its largest segment exponent and its
+//            spacing total; every CTA reads all of them (release/acquire
+//            flags, bounded waits): Emax, Z_{N+1} and the CTA's own spacing
+//            offset follow.
+//   phase 2  the CTA's segment sums on the global grid (unit fixed by
+//            Emax), exact prefixes relative to the CTA range, the CTA total.
+//   exchange 2  every CTA publishes its total and reads all of them: the
+//            CTA prefixes and S.
+//   phase 3  the map of the CTA's own samples: key ceil(U_i S), the owner
+//            CTA of the key by binary search over the CTA prefixes and a
+//            coarse index in shared memory, the segment among 32 prefixes,
+//            the element from the segment's exact prefixes.
+//
+// There is no grid barrier and no per-call clearing: exchange flags carry a
+// per-call epoch kept in device memory (advanced by CTA 0 once every CTA has
+// published its total), so CUDA-graph replays work unchanged.  Every wait is
+// bounded; a wait that runs out latches RS_ETIMEOUT and the kernel finishes
+// (results are then unspecified).  The arithmetic is that of the multi-kernel
+// path (same segment sums, exact integer prefixes, keys and in-segment
+// decisions), so the indices are identical to it.
 #include "map_common.cuh"
+
+// Phase timestamps (profiling builds only, -DGBR_PHASE_STAMPS): %globaltimer
+// of thread 0 (or of lane 0 of warp 0 inside the map) at the phase ends of
+// every CTA, 32 slots per CTA, in a buffer set by rs_dbg_set_stamps.
+#ifdef GBR_PHASE_STAMPS
+namespace gbr {
+__device__ unsigned long long* g_stamps = nullptr;
+}
+extern "C" int rs_dbg_set_stamps(void* p) { return (int)cudaMemcpyToSymbol(gbr::g_stamps, &p, sizeof(p)); }
+#define GBR_STAMP_IF(cond, k)                                              \
+  do {                                                                     \
+    if ((cond) && gbr::g_stamps) {                                         \
+      unsigned long long t_;                                               \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));               \
+      gbr::g_stamps[blockIdx.x * 32 + (k)] = t_;                           \
+    }                                                                      \
+  } while (0)
+#else
+#define GBR_STAMP_IF(cond, k) \
+  do {                        \
+  } while (0)
+#endif
+#define GBR_STAMP(k) GBR_STAMP_IF(threadIdx.x == 0, k)
 
 namespace gbr {
 
 namespace {
 
-constexpr int kFThreads = 256;
+constexpr int kFThreads = 512;
 constexpr int kFWarps = kFThreads / 32;
-constexpr int kCoarseMax = 1024;         // coarse-index entries in shared memory
-constexpr int kMaxCtas = 512;            // CTA prefixes in shared memory
-constexpr int kDynChunk = 4;             // segments per dynamic work item of the weights pass
-static_assert(kFWarps == kMapWarps, "the map phase uses the map's warp layout");
+constexpr int kStages = 3;                 // TMA ring stages
+constexpr int kStageBytes = 64 * 1024;     // 16 binary64 or 32 binary32 segments
+static_assert(kStageBytes < (1 << 20), "an mbarrier phase counts fewer than 2^20 bytes");
+constexpr int kCoarseMax = 1024;           // coarse-index entries in shared memory
+constexpr int kTmaSpin = 1 << 20;          // safety bound of the copy-completion waits
 
 struct FusedArgs {
   const void* w;
-  long long M, nseg, N, ndraw, utiles;
+  long long M, nseg, nfull, N, ndraw;
   unsigned long long seed, inst;
-  SegRec* seg;
-  unsigned* emax_g;   // the largest segment exponent (cleared per call)
-  u128* agg;          // [gridDim.x]
+  SegRec* seg;        // [nseg]
   SegPre* rel;        // [nseg] prefix of each segment relative to its CTA range
-  SegPre* crel;       // [ncoarse] the same for the first segment of each coarse block
-  long long ncoarse, stride;
+  SegPre* crel;       // [ncoarse] the same for every stride-th segment
+  long long ncoarse;
   int lgstride;
-  PathConsts* consts;
-  u128* Z;
-  u128* Ztot;
-  TileDesc<u128>* udesc;
-  unsigned* work;     // work-queue counter (cleared per call)
-  unsigned* bar;      // barrier counter (cleared per call)
+  u128* Z;            // [N] inclusive spacing prefixes relative to the owning CTA's draws
+  unsigned* xch;      // epoch word + exchange slots (kFusedXchBytes)
   int* status;
   int spin;
   bool withhold_first;
   const LogTab* tab;  // logarithm table (binary64 draws)
-  int G;
   int kBS;
   int* out;
 };
 
-__device__ __forceinline__ void grid_sync(unsigned* bar, unsigned& gen, int spin, int* status) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ++gen;
-    __threadfence();
-    atomicAdd(bar, 1u);
-    const unsigned target = gen * gridDim.x;
-    int spins = 0;
-    while (ld_acquire_u32(bar) < target) {
-      if (++spins > spin) {
-        raise_status(status, ST_ETIMEOUT);
-        break;
-      }
-      __nanosleep(32);
-    }
+// Exchange slots: a published value of up to 144 bits travels in three
+// 64-bit words, each carrying the call's 16-bit tag in its low bits.  Aligned
+// 64-bit accesses are single-copy atomic, so a reader that sees the tag in all
+// three words has the whole value in one round trip, without a flag.
+constexpr int kLocalSegs = 1024;  // segment records a CTA keeps in shared memory
+static_assert(kFusedMaxCtas * 2 * 32 + 256 <= kFusedXchBytes, "exchange area");
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void xput(unsigned long long* slot, unsigned tag, u128 v, unsigned extra) {
+  const unsigned long long p0 = v.lo & 0xFFFFFFFFFFFFULL;
+  const unsigned long long p1 = (v.lo >> 48) | ((v.hi & 0xFFFFFFFFULL) << 16);
+  const unsigned long long p2 = (v.hi >> 32) | ((unsigned long long)(extra & 0xFFFFu) << 32);
+  st_relaxed_u64(slot, (p0 << 16) | tag);
+  st_relaxed_u64(slot + 1, (p1 << 16) | tag);
+  st_relaxed_u64(slot + 2, (p2 << 16) | tag);
+}
+// Waits (at most `spin` polls) until all three words carry the tag.
+__device__ __forceinline__ bool xget(const unsigned long long* slot, unsigned tag, int spin, u128& v,
+                                     unsigned& extra) {
+  unsigned long long a0, a1, a2;
+  int spins = 0;
+  while (true) {
+    a0 = ld_relaxed_u64(slot);
+    a1 = ld_relaxed_u64(slot + 1);
+    a2 = ld_relaxed_u64(slot + 2);
+    if ((a0 & 0xFFFFu) == tag && (a1 & 0xFFFFu) == tag && (a2 & 0xFFFFu) == tag) break;
+    if (++spins > spin) return false;
   }
-  __syncthreads();
+  a0 >>= 16;
+  a1 >>= 16;
+  a2 >>= 16;
+  v.lo = a0 | (a1 << 48);
+  v.hi = (a1 >> 16) | ((a2 & 0xFFFFFFFFULL) << 32);
+  extra = (unsigned)(a2 >> 32);
+  return true;
 }
 
-template <int kWarps>
-__device__ __forceinline__ u128 block_sum_u128(u128 v, u128* s_w) {
+__device__ __forceinline__ void st_release_flag(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- mbarrier / bulk-copy helpers (CTA-local) ---------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+// Waits for the phase with the given parity to complete; false after `spin`
+// unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, int spin) {
+  const unsigned a = smem_u32(b);
+  for (int i = 0; i < spin; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// One spacing -log v on the 2^-88 grid, out of line (one copy for the four
+// draws of a Philox block).
+template <bool F32>
+static __device__ __noinline__ u128 spacing_ool(uint64_t word, const LogTab* tab) {
+  return spacing_fixed<F32>(word, tab);
+}
+
+// Owner CTA of segment t under the balanced split floor(nseg c / B).
+__device__ __forceinline__ int seg_owner(long long t, long long nseg, int B) {
+  return (int)(((unsigned long long)(t + 1) * (unsigned)B - 1ULL) / (unsigned long long)nseg);
+}
+
+// Block-wide exclusive prefix of v (over lower thread indices) and total.
+static __device__ __noinline__ void block_scan(u128 v, u128* s_w, u128& excl, u128& tot) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = u128_add(v, shfl_v(v, lane ^ o));
+  const u128 incl = warp_incl_scan_v(v, lane);
+  if (lane == 31) s_w[warp] = incl;
   __syncthreads();
-  if (lane == 0) s_w[warp] = v;
-  __syncthreads();
-  u128 t = {0ULL, 0ULL};
+  u128 before = {0ULL, 0ULL}, t = {0ULL, 0ULL};
 #pragma unroll
-  for (int i = 0; i < kWarps; ++i) t = u128_add(t, s_w[i]);
-  return t;
-}
-
-__device__ __noinline__ void fused_consts(PathConsts* consts, u128 S, long long ge, int Emax, int* status) {
-  consts->S[0] = S.lo;
-  consts->S[1] = S.hi;
-  consts->ge = ge;
-  consts->Emax = Emax;
-  if (u128_is_zero(S)) {
-    raise_status(status, ST_EZEROSUM);
-    consts->c[0] = consts->c[1] = 0ULL;
-    consts->c[2] = (unsigned long long)kXfZeroE;
-    return;
+  for (int i = 0; i < kFWarps; ++i) {
+    const u128 x = s_w[i];
+    if (i < warp) before = u128_add(before, x);
+    t = u128_add(t, x);
   }
-  const xf invZ = {__ldcg(consts->invZ), __ldcg(consts->invZ + 1), (long long)__ldcg(consts->invZ + 2)};
-  const xf c = xf_mul(xf_make(S.hi, S.lo, 0), invZ);
-  consts->c[0] = c.lo;
-  consts->c[1] = c.hi;
-  consts->c[2] = (unsigned long long)c.e;
+  excl = u128_add(before, u128_sub(incl, v));
+  tot = t;
+  __syncthreads();  // s_w may be reused
 }
 
-// The map of the fused kernel: like map_groups, but a sample's segment is
-// found from the coarse index in shared memory (the prefix of every
-// stride-th segment) and then among that block's prefixes, each the CTA
-// prefix plus the segment's prefix relative to its CTA range.
+// ---- the in-segment step of the map, kept small ----------------------------
+// The map after the weights pass is latency-bound and runs once per call, so
+// its code is fetched cold: every step below exists once (no duplicated
+// paths), loops stay rolled, and the segment's exact prefixes are staged in
+// shared memory (slot q*32 + lane holds the prefix of element 16 lane + q)
+// and binary-searched.  Decisions are those of seg_cache_resolve.
+struct LeanSeg {
+  long long cur;
+  u128 Ps, Pn;
+  int sh, len;
+  bool head;
+  unsigned long long F;
+};
+
+__device__ __forceinline__ unsigned long long lean_pref(const unsigned long long* p, int j) {
+  return p[(j & 15) * 32 + (j >> 4)];
+}
+// Number of elements whose exact prefix is below X.
+__device__ __forceinline__ int lean_count(const unsigned long long* p, unsigned long long X) {
+  int lo = 0, hi = kSeg;
+#pragma unroll 1
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lean_pref(p, mid) < X) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+template <bool kVec>
+static __device__ __noinline__ int head_count_ool(const double* w, long long base, long long M, xf rem, int lane) {
+  return head_count<kVec>(w, base, M, rem, lane);
+}
+template <bool kVec>
+static __device__ __noinline__ int head_count_ool(const float*, long long, long long, xf, int) {
+  return 0;
+}
+
+// Makes segment sc (weights b, lane-major; record F, E, len; exclusive
+// prefix Ps) the warp's current one: exact in-segment prefixes to shared
+// memory and the segment's bounds on the global grid.
+template <typename T>
+__device__ __forceinline__ void lean_fill(LeanSeg& c, const typename FixedTraits<T>::Bits (&b)[kSegV],
+                                          unsigned long long F, int E, int len, long long sc, const u128& Ps,
+                                          int Emax, unsigned long long* my_pref, int lane) {
+  uint64_t pref[kSegV];
+  seg_prefixes<T>(b, (uint32_t)E, lane, pref);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < kSegV; ++q) my_pref[q * 32 + lane] = pref[q];
+  __syncwarp();
+  c.cur = sc;
+  c.F = F;
+  c.len = len;
+  c.Ps = Ps;
+  c.Pn = u128_add(Ps, grid_value(F, E, Emax));
+  c.sh = E - Emax + kGridHead;
+  const xf Px = xf_make(Ps.hi, Ps.lo, 0);
+  c.head = sizeof(T) == 8 && (xf_zero(Px) || Px.e + kXfTop < (long long)c.sh + 50);
+}
+
+// Resolves one round: every valid lane has its segment s_me and that
+// segment's exclusive prefix P_me; lanes sharing a segment are contiguous.
+// The next distinct segment's weights are copied to my_buf (asynchronously)
+// while the current one is resolved.
 template <typename T, bool kVec>
-__device__ __forceinline__ void map_groups_direct(const T* __restrict__ w, long long M,
-                                                  const SegRec* __restrict__ seg, const SegPre* __restrict__ rel,
-                                                  long long nseg, const u128* __restrict__ Z, long long N, int G,
-                                                  const MapCtx& cx, const u128* s_cp, const u128* s_coarse,
-                                                  const short* s_ccta, long long ncoarse, long long stride,
-                                                  typename FixedTraits<T>::Bits* my_buf, long long g_first,
-                                                  long long g_stride, int* __restrict__ out) {
+__device__ __forceinline__ void lean_round(LeanSeg& c, const T* __restrict__ w, long long M,
+                                           const SegRec* __restrict__ seg, bool valid, long long s_me, const u128& P_me,
+                                           const u128& key, long long i, int Emax, long long ge,
+                                           unsigned long long* my_pref, typename FixedTraits<T>::Bits* my_buf, int lane,
+                                           int* __restrict__ out) {
+  using Bits = typename FixedTraits<T>::Bits;
+  unsigned pend = __ballot_sync(0xFFFFFFFFu, valid);
+  long long pf = -1;  // segment being copied to my_buf
+  unsigned long long pfF = 0;
+  int pfE = 0, pfL = 0;
+#pragma unroll 1
+  while (pend) {
+    const int l0 = __ffs(pend) - 1;
+    const long long sc = __shfl_sync(0xFFFFFFFFu, s_me, l0);
+    const u128 Psc = shfl_v(P_me, l0);
+    const unsigned grp = __ballot_sync(0xFFFFFFFFu, valid && s_me == sc) & pend;
+    const unsigned rest = pend & ~grp;
+    if (sc != c.cur) {
+      Bits b[kSegV];
+      unsigned long long F;
+      int E, len;
+      if (sc == pf) {
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kSegV; ++q) b[q] = my_buf[lane * kSegV + q];
+        F = pfF;
+        E = pfE;
+        len = pfL;
+        pf = -1;
+        __syncwarp();  // my_buf is free again
+      } else {
+        F = __ldcg(&seg[sc].F);
+        E = __ldcg(&seg[sc].E);
+        len = __ldcg(&seg[sc].len);
+        load_seg_blocked<T, kVec>(w, sc * kSeg, M, lane, b);
+      }
+      if (kVec && rest) {
+        const long long sn = __shfl_sync(0xFFFFFFFFu, s_me, __ffs(rest) - 1);
+        if ((sn + 1) * kSeg <= M) {
+          seg_prefetch<T>(w, sn, lane, my_buf);
+          pf = sn;
+          pfF = __ldcg(&seg[sn].F);
+          pfE = __ldcg(&seg[sn].E);
+          pfL = __ldcg(&seg[sn].len);
+        }
+      }
+      lean_fill<T>(c, b, F, E, len, sc, Psc, Emax, my_pref, lane);
+    }
+    // the element: first whose exact prefix reaches K = ceil(rem / unit_s)
+    const bool mine = (grp >> lane) & 1u;
+    const u128 rem = (mine && u128_lt(c.Ps, key)) ? u128_sub(key, c.Ps) : u128{0ULL, 0ULL};
+    bool small = false;
+    if (c.head && mine) {
+      const xf rx = xf_make(rem.hi, rem.lo, 0);
+      small = xf_zero(rx) || rx.e + kXfTop < (long long)c.sh + 50;
+    }
+    const unsigned long long K = ceil_units(rem, c.sh, c.F);
+    int cnt = mine ? lean_count(my_pref, K) : 0;
+    if (__any_sync(0xFFFFFFFFu, small)) {
+      // head segment: the grid count is exact unless a grid prefix lies in
+      // [K - len, K) or K was clamped at the segment total
+      bool amb = false;
+      if (small) {
+        if (K >= c.F) amb = true;
+        else if ((long long)K <= c.len) amb = cnt > 0;
+        else amb = lean_count(my_pref, K - (unsigned long long)c.len) != cnt;
+      }
+      unsigned gx = __ballot_sync(0xFFFFFFFFu, small && amb);
+#pragma unroll 1
+      while (gx) {
+        const int jl = __ffs(gx) - 1;
+        gx &= gx - 1;
+        const u128 rj = shfl_v(rem, jl);
+        const int cj = head_count_ool<kVec>(w, sc * kSeg, M, xf_make(rj.hi, rj.lo, ge), lane);
+        if (lane == jl) cnt = cj;
+      }
+    }
+    if (mine) {
+      const long long j = cnt < c.len ? cnt : c.len - 1;
+      long long rr = sc * kSeg + j;
+      if (rr > M - 1) rr = M - 1;
+      out[i] = (int)rr;
+    }
+    pend = rest;
+  }
+  if (pf >= 0) cp_async_wait_all();  // nothing in flight when the buffer is next used
+}
+
+// The map of the CTA's own samples [i0, i1) by one warp, in rounds of 32:
+// keys, the segment among the prefixes P_t = (CTA prefix of t's owner) + rel_t,
+// located through the coarse index, then the in-segment decision.
+template <typename T, bool kVec>
+__device__ __forceinline__ void map_own(const T* __restrict__ w, long long M, const SegRec* __restrict__ seg,
+                                        const SegPre* __restrict__ rel, long long nseg, const u128* __restrict__ Z,
+                                        u128 zoff, u128 z_first, long long i0, long long i1, const MapCtx& cx,
+                                        const u128* s_cp,
+                                        const u128* s_coarse, long long ncoarse, int lgstride, int B,
+                                        typename FixedTraits<T>::Bits* my_buf, int* __restrict__ out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long* my_pref = cx.s_pref + warp * kSeg;
   u128* my_win = cx.s_win + warp * 32;
   const u128 kInf = {~0ULL, ~0ULL};
-  for (long long g = g_first; g * (long long)G < N; g += g_stride) {
-    const long long i0 = g * (long long)G;
-    const long long i1 = (i0 + G < N) ? i0 + G : N;
-    SegCache c;
-    seg_cache_init(c);
-    for (long long r0 = i0; r0 < i1; r0 += 32) {
-      const long long i = r0 + lane;
-      const bool valid = i < i1;
-      u128 key = {0ULL, 0ULL};
-      if (valid) key = map_key(cx.c, u128{__ldcg(&Z[i].lo), __ldcg(&Z[i].hi)});  // ceil(U_i * S) in grid units
-      const bool in_cur = valid && c.cur >= 0 && u128_lt(c.Ps, key) && !u128_lt(c.Pn, key);
-      long long s_me = c.cur;
-      u128 P_me = c.Ps;
-      unsigned need = __ballot_sync(0xFFFFFFFFu, valid && !in_cur);
-      if (need) {
-        // coarse block: the last j with coarse_j < key (coarse_0 = 0 < key)
-        long long j_me = 0;
-        if ((need >> lane) & 1u) {
-          long long lo = 0, hi = ncoarse;
-          while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if (u128_lt(s_coarse[mid], key)) lo = mid + 1;
-            else hi = mid;
-          }
-          j_me = lo > 0 ? lo - 1 : 0;
+  const long long stride = 1LL << lgstride;
+  LeanSeg c;
+  c.cur = -1;
+  c.Ps = c.Pn = u128{0ULL, 0ULL};
+  c.sh = c.len = 0;
+  c.head = false;
+  c.F = 0;
+#pragma unroll 1
+  for (long long r0 = i0; r0 < i1; r0 += 32) {
+    const long long i = r0 + lane;
+    const bool valid = i < i1;
+    const bool w0 = threadIdx.x == 0 && r0 == i0;
+    GBR_STAMP_IF(w0, 10);
+    u128 key = {0ULL, 0ULL};
+    if (valid) key = map_key(cx.c, u128_add(zoff, r0 == i0 ? z_first : u128{__ldcg(&Z[i].lo), __ldcg(&Z[i].hi)}));
+    GBR_STAMP_IF(w0, 11);
+    const bool in_cur = valid && c.cur >= 0 && u128_lt(c.Ps, key) && !u128_lt(c.Pn, key);
+    long long s_me = c.cur;
+    u128 P_me = c.Ps;
+    unsigned need = __ballot_sync(0xFFFFFFFFu, valid && !in_cur);
+    if (need) {
+      // coarse block: the last j with coarse_j < key (coarse_0 = 0 < key)
+      long long j_me = 0;
+      if ((need >> lane) & 1u) {
+        long long lo = 0, hi = ncoarse;
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (u128_lt(s_coarse[mid], key)) lo = mid + 1;
+          else hi = mid;
         }
-        while (need) {
-          const long long jj = __shfl_sync(0xFFFFFFFFu, j_me, __ffs(need) - 1);
-          const unsigned grp = __ballot_sync(0xFFFFFFFFu, ((need >> lane) & 1u) && j_me == jj) & need;
-          const int bcta = s_ccta[jj];
-          const u128 cpb = s_cp[bcta];
-          const long long blo = jj * stride;
-          const long long bhi = blo + stride < nseg ? blo + stride : nseg;
-          unsigned unres = grp;
-          u128 prevP = kInf;  // prefix of segment c0 - 1
-          // the block's prefixes, 32 at a time (one load per lane)
-          for (long long c0 = blo; c0 < bhi && unres; c0 += 32) {
-            const long long t = c0 + lane;
-            u128 Pt = kInf;
-            if (t < bhi) Pt = u128_add(cpb, u128{__ldcg(&rel[t].lo), __ldcg(&rel[t].hi)});
-            my_win[lane] = Pt;
-            __syncwarp();
-            // a sample is resolved in the batch holding the first prefix that
-            // reaches its key; the block's last batch also takes keys above
-            // every prefix (the block's end, or S plus rounding)
-            const bool last_batch = c0 + 32 >= bhi;
-            bool here = false;
-            if ((unres >> lane) & 1u) {
-              int l2 = 0, h2 = 32;
-              while (l2 < h2) {
-                const int mid = (l2 + h2) >> 1;
-                if (u128_lt(my_win[mid], key)) l2 = mid + 1;
-                else h2 = mid;
-              }
-              here = l2 < 32 || last_batch;
-              if (here) {
-                if (l2 > 0) {
-                  s_me = c0 + l2 - 1;
-                  P_me = my_win[l2 - 1];
-                } else {  // the batch's first prefix already reaches the key
-                  s_me = c0 - 1;
-                  P_me = prevP;
-                }
+        j_me = lo > 0 ? lo - 1 : 0;
+      }
+      while (need) {
+        const long long jj = __shfl_sync(0xFFFFFFFFu, j_me, __ffs(need) - 1);
+        const unsigned grp = __ballot_sync(0xFFFFFFFFu, ((need >> lane) & 1u) && j_me == jj) & need;
+        const long long blo = jj * stride;
+        const long long bhi = blo + stride < nseg ? blo + stride : nseg;
+        unsigned unres = grp;
+        u128 prevP = kInf;  // prefix of segment c0 - 1
+        for (long long c0 = blo; c0 < bhi && unres; c0 += 32) {
+          const long long t = c0 + lane;
+          u128 Pt = kInf;
+          if (t < bhi) Pt = u128_add(s_cp[seg_owner(t, nseg, B)], u128{__ldcg(&rel[t].lo), __ldcg(&rel[t].hi)});
+          my_win[lane] = Pt;
+          __syncwarp();
+          // a sample is resolved in the batch holding the first prefix that
+          // reaches its key; the block's last batch also takes keys above
+          // every prefix (the block's end, or S plus rounding)
+          const bool last_batch = c0 + 32 >= bhi;
+          bool here = false;
+          if ((unres >> lane) & 1u) {
+            int l2 = 0, h2 = 32;
+            while (l2 < h2) {
+              const int mid = (l2 + h2) >> 1;
+              if (u128_lt(my_win[mid], key)) l2 = mid + 1;
+              else h2 = mid;
+            }
+            here = l2 < 32 || last_batch;
+            if (here) {
+              if (l2 > 0) {
+                s_me = c0 + l2 - 1;
+                P_me = my_win[l2 - 1];
+              } else {  // the batch's first prefix already reaches the key
+                s_me = c0 - 1;
+                P_me = prevP;
               }
             }
-            unres &= ~__ballot_sync(0xFFFFFFFFu, here);
-            prevP = my_win[31];
-            __syncwarp();
           }
-          need &= ~grp;
+          unres &= ~__ballot_sync(0xFFFFFFFFu, here);
+          prevP = my_win[31];
+          __syncwarp();
         }
+        need &= ~grp;
       }
-      resolve_round<T, kVec>(c, w, M, seg, valid, s_me, P_me, key, i, cx, my_pref, lane, out,
-                             my_buf + (long long)warp * kSeg);
+      if (s_me < 0) {  // only a zero key (all weights zero): the first segment
+        s_me = 0;
+        P_me = u128{0ULL, 0ULL};
+      }
     }
+    GBR_STAMP_IF(w0, 12);
+    lean_round<T, kVec>(c, w, M, seg, valid, s_me, P_me, key, i, cx.Emax, cx.ge, my_pref,
+                        my_buf + (long long)warp * kSeg, lane, out);
+    GBR_STAMP_IF(w0, 13);
   }
 }
 
 }  // namespace
 
 template <typename T, bool kVec>
-__global__ void __launch_bounds__(kFThreads, 2) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   constexpr bool F32 = sizeof(T) == 4;
   using Bits = typename FixedTraits<T>::Bits;
-  extern __shared__ __align__(16) unsigned long long s_dyn[];  // map staging
+  constexpr int kSegBytes = kSeg * (int)sizeof(T);
+  constexpr int kStageSegs = kStageBytes / kSegBytes;
+  constexpr int kSegsPerWarp = kStageSegs / kFWarps;
+  extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ LogTab tab;
-  __shared__ UniformTileSmem us;
-  __shared__ int s_e[kFWarps];
   __shared__ u128 s_w[kFWarps];
-  __shared__ xf s_c;
-  __shared__ u128 s_S;
-  __shared__ long long s_ge;
+  __shared__ unsigned long long s_full[kStages], s_empty[kStages];
+  __shared__ int s_e[kFWarps], s_x[kFWarps];
+  __shared__ xf s_c, s_invZ;
+  __shared__ u128 s_S, s_zoff;
   __shared__ int s_Emax;
+  __shared__ unsigned s_target;
+  __shared__ unsigned long long s_lF[kLocalSegs];  // the CTA's segment records, when they fit
+  __shared__ int s_lE[kLocalSegs];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int B = gridDim.x, cta = blockIdx.x;
   const T* w = static_cast<const T*>(a.w);
-  unsigned gen = 0;
+  unsigned long long* x1 = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(a.xch) + 256);
+  unsigned long long* x2 = x1 + 4 * kFusedMaxCtas;
+
+  // ranges of this CTA
+  const long long s0 = a.nseg * cta / B, s1 = a.nseg * (cta + 1) / B;
+  const long long d0 = a.ndraw * cta / B, d1 = a.ndraw * (cta + 1) / B;
+  const long long tma_end = s1 < a.nfull ? s1 : (s0 > a.nfull ? s0 : a.nfull);  // full segments [s0, tma_end)
+  const long long n_it = kVec ? (tma_end - s0 + kStageSegs - 1) / kStageSegs : 0;
+  const bool local = s1 - s0 <= kLocalSegs;
+
+  if (tid == 0) {
+    s_target = __ldcg(a.xch) + 1u;  // this call's epoch
+    if (kVec) {
+      for (int s = 0; s < kStages; ++s) {
+        mbar_init(&s_full[s], 1);
+        mbar_init(&s_empty[s], kFWarps);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;\n fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
   if (!F32)
     for (int i = tid; i < 129; i += kFThreads) {
       tab.nlogc[i] = a.tab->nlogc[i];
       tab.invc[i] = a.tab->invc[i];
     }
   __syncthreads();
+  const unsigned target = s_target;
+  const unsigned tag = target % 65535u + 1u;  // never 0 (a slot never written), differs between calls
+  GBR_STAMP(0);
 
-  // ---- phase 1: spacing tiles, then segment sums ------------------------------
-  // spacing tiles by CTA index: a tile waits only on lower tiles, which every
-  // CTA processes in increasing order, so every wait ends
-  const int B = gridDim.x;
-  for (long long t = blockIdx.x; t < a.utiles; t += B)
-    uniform_tile<F32>(t, a.ndraw, a.seed, a.inst, a.Z, a.Ztot, a.consts, a.udesc, a.status, a.spin,
-                      a.withhold_first, &tab, us);
-  // segments: a static round-robin share (half), then chunks of kDynChunk from
-  // a shared counter; the next segment's loads are issued before the current
-  // one is reduced.  When only some CTAs drew spacing tiles, the static share
-  // goes to the others.
-  int emax = 0;
+  // stage it of the ring: segments [s0 + it*kStageSegs, ...) of the CTA range
+  auto issue = [&](long long it) {
+    const int st = (int)(it % kStages);
+    const long long sa = s0 + it * kStageSegs;
+    const long long sb = sa + kStageSegs < tma_end ? sa + kStageSegs : tma_end;
+    const unsigned bytes = (unsigned)((sb - sa) * kSegBytes);
+    mbar_expect_tx(&s_full[st], bytes);
+    bulk_g2s(s_dyn + (size_t)st * kStageBytes, w + sa * kSeg, bytes, &s_full[st]);  // one copy per stage
+  };
+  if (kVec && tid == 0)
+    for (long long it = 0; it < n_it && it < kStages; ++it) issue(it);
+  GBR_STAMP(14);
+  if (tid == kFThreads - 32) {
+    // fetch the code of the once-per-call scalar steps (reciprocal, product)
+    // into the instruction caches while the first copies are in flight
+    const xf r = recip_total(u128{(unsigned long long)a.M | 1ULL, 0ULL});
+    if (r.lo == 0x5A5A5A5AULL && r.hi == (unsigned long long)a.N) s_c = r;  // never true; keeps the call
+  }
+
+  // ---- phase 1a: the CTA's draws (Algorithm 1) -------------------------------
+  u128 ztot = {0ULL, 0ULL};
   {
-    const long long ub = a.utiles < B ? a.utiles : 0;  // CTAs left out of the static share
-    const long long W = ((long long)B - ub) * kFWarps;
-    const long long gw = ((long long)blockIdx.x - ub) * kFWarps + warp;
-    const long long per = (long long)blockIdx.x < ub ? 0 : (a.nseg / 2) / W;
-    const long long pool = ((a.nseg / 2) / W) * W;
-    long long k = 0, dyn_s = 0, dyn_left = 0;
-    auto next_seg = [&]() -> long long {
-      if (k < per) return gw + (k++) * W;
-      if (dyn_left == 0) {
-        unsigned c = 0;
-        if (lane == 0) c = atomicAdd(a.work, 1u);
-        c = __shfl_sync(0xFFFFFFFFu, c, 0);
-        dyn_s = pool + (long long)c * kDynChunk;
-        dyn_left = kDynChunk;
-      }
-      --dyn_left;
-      return dyn_s++;
-    };
-    long long cur = next_seg();
-    Bits cb[kSegV];
-    if (cur < a.nseg) load_seg_striped<T, kVec>(w, cur * kSeg, a.M, lane, cb);
-    while (cur < a.nseg) {
-      const long long nxt = next_seg();
-      Bits nb[kSegV];
-      if (nxt < a.nseg) load_seg_striped<T, kVec>(w, nxt * kSeg, a.M, lane, nb);
-      uint64_t F;
-      uint32_t E;
-      seg_sum_bits<T>(cb, lane, a.status, F, E);
-      if (lane == 0) {
-        const long long rem = a.M - cur * kSeg;
-        a.seg[cur] = SegRec{F, (int)E, (int)(rem < kSeg ? rem : kSeg)};
-      }
-      emax = max(emax, (int)E);
-      cur = nxt;
+    const long long base = d0 & ~3LL;
+#pragma unroll 1
+    for (long long t0 = base; t0 < d1; t0 += 4LL * kFThreads) {
+      const long long k0 = t0 + 4LL * tid;
+      u128 pre[4];
+      u128 run = {0ULL, 0ULL};
+      if (k0 < d1 && k0 + 3 >= d0) {
+        uint64_t words[4];
+        philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
 #pragma unroll
-      for (int q = 0; q < kSegV; ++q) cb[q] = nb[q];
+        for (int q = 0; q < 4; ++q) {
+          const long long k = k0 + q;
+          if (k >= d0 && k < d1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
+          pre[q] = run;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pre[q] = run;
+      }
+      u128 excl, tot;
+      block_scan(run, s_w, excl, tot);
+      excl = u128_add(excl, ztot);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long k = k0 + q;
+        if (k >= d0 && k < d1 && k < a.N) a.Z[k] = u128_add(excl, pre[q]);
+      }
+      ztot = u128_add(ztot, tot);
     }
+  }
+  GBR_STAMP(1);
+
+  // ---- phase 1b: the CTA's segments ------------------------------------------
+  int emax = 0;
+  if (kVec) {
+#pragma unroll 1
+    for (long long it = 0; it < n_it; ++it) {
+      const int st = (int)(it % kStages);
+      const unsigned par = (unsigned)((it / kStages) & 1);
+      if (!mbar_wait(&s_full[st], par, kTmaSpin)) {
+        if (lane == 0) raise_status(a.status, ST_ETIMEOUT);
+        mbar_wait(&s_full[st], par, kTmaSpin);  // the copy is still owed: wait again, bounded
+      }
+      const long long sa = s0 + it * kStageSegs;
+#pragma unroll
+      for (int r = 0; r < kSegsPerWarp; ++r) {
+        const int j = warp + r * kFWarps;
+        const long long s = sa + j;
+        if (s < tma_end) {
+          const unsigned char* src = s_dyn + (size_t)st * kStageBytes + (size_t)j * kSegBytes;
+          Bits b[kSegV];
+          constexpr int kPer = 16 / (int)sizeof(T);  // elements per 16-byte piece
+#pragma unroll
+          for (int q = 0; q < kSegV / kPer; ++q) {
+            const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * lane + 512 * q);
+            if (F32) {
+              b[4 * q] = (Bits)v.x;
+              b[4 * q + 1] = (Bits)v.y;
+              b[4 * q + 2] = (Bits)v.z;
+              b[4 * q + 3] = (Bits)v.w;
+            } else {
+              b[2 * q] = (Bits)(((uint64_t)v.y << 32) | v.x);
+              b[2 * q + 1] = (Bits)(((uint64_t)v.w << 32) | v.z);
+            }
+          }
+          uint64_t F;
+          uint32_t E;
+          seg_sum_bits<T>(b, lane, a.status, F, E);
+          if (lane == 0) {
+            a.seg[s] = SegRec{F, (int)E, kSeg};
+            if (local) {
+              s_lF[s - s0] = F;
+              s_lE[s - s0] = (int)E;
+            }
+          }
+          emax = max(emax, (int)E);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s_empty[st]);
+      if (tid == 0 && it + kStages < n_it) {
+        // refill this stage once every warp has read it
+        if (!mbar_wait(&s_empty[st], par, kTmaSpin)) raise_status(a.status, ST_ETIMEOUT);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(it + kStages);
+      }
+    }
+  }
+  // segments not taken by the ring (unaligned weights, the ragged last one)
+#pragma unroll 1
+  for (long long s = (kVec ? tma_end : s0) + warp; s < s1; s += kFWarps) {
+    Bits b[kSegV];
+    load_seg_striped<T, kVec>(w, s * kSeg, a.M, lane, b);
+    uint64_t F;
+    uint32_t E;
+    seg_sum_bits<T>(b, lane, a.status, F, E);
+    if (lane == 0) {
+      const long long rem = a.M - s * kSeg;
+      a.seg[s] = SegRec{F, (int)E, (int)(rem < kSeg ? rem : kSeg)};
+      if (local) {
+        s_lF[s - s0] = F;
+        s_lE[s - s0] = (int)E;
+      }
+    }
+    emax = max(emax, (int)E);
   }
   if (lane == 0) s_e[warp] = emax;
   __syncthreads();
+  GBR_STAMP(2);
+
+  // ---- exchange 1: segment exponents and spacing totals ----------------------
+  // (nothing else of this CTA is read by others before exchange 2, whose
+  // writer fence covers it)
   if (tid == 0) {
     int m = 0;
 #pragma unroll
     for (int i = 0; i < kFWarps; ++i) m = max(m, s_e[i]);
-    atomicMax(a.emax_g, (unsigned)m);
+    if (!(a.withhold_first && cta == 0)) xput(x1 + 4 * cta, tag, ztot, (unsigned)m);
+    GBR_STAMP(25);
   }
-  grid_sync(a.bar, gen, a.spin, a.status);
-
-  // ---- phase 2: grid values of this CTA's segment range ----------------------
-  const int Emax = (int)__ldcg(a.emax_g);
   {
-    // consecutive sub-ranges per thread; exclusive scan inside the CTA gives
-    // every segment's prefix relative to the CTA range's start
-    // the CTA owns whole coarse blocks: [jlo, jhi) of stride segments each
-    const int nc = (int)a.ncoarse;  // <= kCoarseMax: 32-bit division
-    const int jlo = nc * (int)blockIdx.x / B, jhi = nc * ((int)blockIdx.x + 1) / B;
-    const long long lo = (long long)jlo * a.stride;
-    const long long hi = (long long)jhi * a.stride < a.nseg ? (long long)jhi * a.stride : a.nseg;
-    const long long t_lo = lo + (hi - lo) * tid / kFThreads, t_hi = lo + (hi - lo) * (tid + 1) / kFThreads;
-    u128 tsum = {0ULL, 0ULL};
-    for (long long s = t_lo; s < t_hi; ++s)
-      tsum = u128_add(tsum, grid_value(__ldcg(&a.seg[s].F), __ldcg(&a.seg[s].E), Emax));
-    const u128 incl = warp_incl_scan_v(tsum, lane);
-    __syncthreads();
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    u128 R = u128_sub(incl, tsum), ctot = {0ULL, 0ULL};
-#pragma unroll
-    for (int i = 0; i < kFWarps; ++i) {
-      if (i < warp) R = u128_add(R, s_w[i]);
-      ctot = u128_add(ctot, s_w[i]);
+    unsigned e = 0;
+    u128 z = {0ULL, 0ULL};
+    if (tid < B && !xget(x1 + 4 * tid, tag, a.spin, z, e)) {
+      raise_status(a.status, ST_ETIMEOUT);
+      e = 0;
+      z = u128{0ULL, 0ULL};
     }
+    GBR_STAMP(24);
+    const int wm = (int)__reduce_max_sync(0xFFFFFFFFu, e);
+    GBR_STAMP(8);
+    if (lane == 0) s_x[warp] = wm;
+    u128 excl, tot;
+    block_scan(z, s_w, excl, tot);  // (its __syncthreads also publishes s_x)
+    if (tid == cta) s_zoff = excl;  // spacing totals of the CTAs before this one
+    if (tid == 0) {
+      int m = 0;
+#pragma unroll
+      for (int i = 0; i < kFWarps; ++i) m = max(m, s_x[i]);
+      s_Emax = m;
+      s_S = tot;  // Z_{N+1}, until the reciprocal is taken
+    }
+    __syncthreads();
+  }
+  GBR_STAMP(3);
+
+  // ---- phase 2: the CTA range on the global grid -----------------------------
+  const int Emax = s_Emax;
+  const long long stride = 1LL << a.lgstride;
+  {
+    const long long n = s1 - s0;
+    const long long t_lo = s0 + n * tid / kFThreads, t_hi = s0 + n * (tid + 1) / kFThreads;
+    u128 tsum = {0ULL, 0ULL};
+#pragma unroll 1
+    for (long long s = t_lo; s < t_hi; ++s) {
+      const unsigned long long F = local ? s_lF[s - s0] : __ldcg(&a.seg[s].F);
+      const int E = local ? s_lE[s - s0] : __ldcg(&a.seg[s].E);
+      tsum = u128_add(tsum, grid_value(F, E, Emax));
+    }
+    GBR_STAMP(20);
+    u128 R, ctot;
+    block_scan(tsum, s_w, R, ctot);
+    GBR_STAMP(21);
+#pragma unroll 1
     for (long long s = t_lo; s < t_hi; ++s) {
       a.rel[s] = SegPre{R.lo, R.hi};
-      if ((s & (a.stride - 1)) == 0) a.crel[s >> a.lgstride] = SegPre{R.lo, R.hi};
-      R = u128_add(R, grid_value(__ldcg(&a.seg[s].F), __ldcg(&a.seg[s].E), Emax));
+      if ((s & (stride - 1)) == 0) a.crel[s >> a.lgstride] = SegPre{R.lo, R.hi};
+      const unsigned long long F = local ? s_lF[s - s0] : __ldcg(&a.seg[s].F);
+      const int E = local ? s_lE[s - s0] : __ldcg(&a.seg[s].E);
+      R = u128_add(R, grid_value(F, E, Emax));
     }
-    if (tid == 0) a.agg[blockIdx.x] = ctot;
+    __syncthreads();  // rel, crel and the segment records precede the published total
+    GBR_STAMP(22);
+    if (tid == 0) {
+      __threadfence();
+      GBR_STAMP(23);
+      xput(x2 + 4 * cta, tag, ctot, 0u);
+      GBR_STAMP(15);
+      // 1 / Z_{N+1} while the other CTAs finish
+      const u128 zt = s_S;
+      s_invZ = u128_is_zero(zt) ? lb_zero<xf>() : recip_total(zt);
+      GBR_STAMP(9);
+    }
   }
-  grid_sync(a.bar, gen, a.spin, a.status);
+  GBR_STAMP(4);
 
-  // ---- phase 3: CTA prefixes, S, S / Z_{N+1}; the map -------------------------
-  u128* s_cp = reinterpret_cast<u128*>(s_dyn + kMapWarps * kSeg + kMapWarps * 32 * 2);  // [B + 1]
-  u128* s_coarse = s_cp + (kMaxCtas + 1);                                                   // [ncoarse]
-  short* s_ccta = reinterpret_cast<short*>(s_coarse + kCoarseMax);                          // CTA of each entry
+  // this warp's samples and the spacing prefixes of their first round, read
+  // before the exchange completes
+  const long long m0 = d0, m1 = d1 < a.N ? d1 : a.N;
+  const long long nsm = m1 > m0 ? m1 - m0 : 0;
+  const long long i0 = m0 + nsm * warp / kFWarps, i1 = m0 + nsm * (warp + 1) / kFWarps;
+  u128 z_first = {0ULL, 0ULL};
+  if (i0 + lane < i1) z_first = u128{__ldcg(&a.Z[i0 + lane].lo), __ldcg(&a.Z[i0 + lane].hi)};
+
+  // ---- exchange 2: CTA totals -> CTA prefixes and S --------------------------
+  u128* s_cp = reinterpret_cast<u128*>(s_dyn);          // [B + 1]
+  u128* s_coarse = s_cp + (kFusedMaxCtas + 1);          // [ncoarse]
+  unsigned long long* s_pref = reinterpret_cast<unsigned long long*>(s_coarse + kCoarseMax);  // kFWarps x 512
+  u128* s_win = reinterpret_cast<u128*>(s_pref + kFWarps * kSeg);                           // kFWarps x 32
+  Bits* s_buf = reinterpret_cast<Bits*>(s_win + kFWarps * 32);                              // kFWarps x 512
   {
-    // the coarse entries' relative prefixes go to shared memory while the CTA
-    // totals are scanned; each thread then adds the CTA prefix to the entries
-    // of CTAs 2 tid and 2 tid + 1
-    const int t0 = 2 * tid;
-    for (long long j = tid; j < a.ncoarse; j += kFThreads)
-      s_coarse[j] = u128{__ldcg(&a.crel[j].lo), __ldcg(&a.crel[j].hi)};
-    const u128 v0 = t0 < B ? u128{__ldcg(&a.agg[t0].lo), __ldcg(&a.agg[t0].hi)} : u128{0ULL, 0ULL};
-    const u128 v1 = t0 + 1 < B ? u128{__ldcg(&a.agg[t0 + 1].lo), __ldcg(&a.agg[t0 + 1].hi)} : u128{0ULL, 0ULL};
-    xf invZ = lb_zero<xf>();
-    if (tid == 0) invZ = xf{__ldcg(a.consts->invZ), __ldcg(a.consts->invZ + 1), (long long)__ldcg(a.consts->invZ + 2)};
-    const u128 pair = u128_add(v0, v1);
-    const u128 incl = warp_incl_scan_v(pair, lane);
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    u128 off = u128_sub(incl, pair), tot = {0ULL, 0ULL};
-#pragma unroll
-    for (int i = 0; i < kFWarps; ++i) {
-      if (i < warp) off = u128_add(off, s_w[i]);
-      tot = u128_add(tot, s_w[i]);
-    }
-    const u128 cpq[2] = {off, u128_add(off, v0)};
-    if (tid == 0) {  // S / Z_{N+1} while the others place the coarse entries
-      s_S = tot;
-      s_c = u128_is_zero(tot) ? lb_zero<xf>() : xf_mul(xf_make(tot.hi, tot.lo, 0), invZ);
-    }
-    __syncthreads();  // the relative entries are in place
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int b = t0 + q;
-      if (b < B) {
-        s_cp[b] = cpq[q];
-        const int jl = (int)a.ncoarse * b / B, jh = (int)a.ncoarse * (b + 1) / B;
-        for (int j = jl; j < jh; ++j) {
-          s_coarse[j] = u128_add(cpq[q], s_coarse[j]);
-          s_ccta[j] = (short)b;
-        }
+    unsigned e = 0;
+    u128 v = {0ULL, 0ULL};
+    if (tid < B) {
+      if (!xget(x2 + 4 * tid, tag, a.spin, v, e)) {
+        raise_status(a.status, ST_ETIMEOUT);
+        v = u128{0ULL, 0ULL};
       }
+      GBR_STAMP(16);
+      __threadfence();  // acquire: the publishers' segment data are read below
+      GBR_STAMP(17);
     }
-    if (tid == 0) s_cp[B] = tot;
-    if (tid == 32 && blockIdx.x == 0) fused_consts(a.consts, tot, (long long)Emax - a.kBS - kGridHead, Emax, a.status);
+    u128 excl, tot;
+    block_scan(v, s_w, excl, tot);
+    GBR_STAMP(18);
+    if (tid < B) s_cp[tid] = excl;
+    if (tid == 0) {
+      s_cp[B] = tot;
+      s_S = tot;
+      if (u128_is_zero(tot)) {
+        if (cta == 0) raise_status(a.status, ST_EZEROSUM);
+        s_c = lb_zero<xf>();
+      } else {
+        s_c = xf_mul_ool(xf_make(tot.hi, tot.lo, 0), s_invZ);
+      }
+      GBR_STAMP(19);
+      // every CTA has read this call's epoch (its totals are in): advance it
+      if (cta == 0) st_release_flag(a.xch, target);
+    }
+    __syncthreads();
+    GBR_STAMP(5);
+#pragma unroll 1
+    for (long long j = tid; j < a.ncoarse; j += kFThreads)
+      s_coarse[j] = u128_add(s_cp[seg_owner(j << a.lgstride, a.nseg, B)],
+                             u128{__ldcg(&a.crel[j].lo), __ldcg(&a.crel[j].hi)});
     __syncthreads();
   }
+  GBR_STAMP(6);
+
+  // ---- phase 3: the map of this CTA's samples --------------------------------
   MapCtx cx;
   cx.s_top = nullptr;
   cx.ntop = 0;
-  cx.s_pref = s_dyn;
-  cx.s_win = reinterpret_cast<u128*>(s_dyn + kMapWarps * kSeg);
+  cx.s_pref = s_pref;
+  cx.s_win = s_win;
   cx.c = s_c;
   cx.S = s_S;
   cx.ge = (long long)Emax - a.kBS - kGridHead;
   cx.Emax = Emax;
-  Bits* s_buf = reinterpret_cast<Bits*>(s_ccta + kCoarseMax);  // kMapWarps x 512 prefetched weights
-  map_groups_direct<T, kVec>(w, a.M, a.seg, a.rel, a.nseg, a.Z, a.N, a.G, cx, s_cp, s_coarse, s_ccta, a.ncoarse,
-                             a.stride, s_buf, (long long)blockIdx.x * kFWarps + warp, (long long)gridDim.x * kFWarps,
-                             a.out);
+  if (i1 > i0)
+    map_own<T, kVec>(w, a.M, a.seg, a.rel, a.nseg, a.Z, s_zoff, z_first, i0, i1, cx, s_cp, s_coarse, a.ncoarse,
+                     a.lgstride, B, s_buf, a.out);
+#ifdef GBR_PHASE_STAMPS
+  __syncthreads();
+  GBR_STAMP(7);
+#endif
+}
+
+size_t fused_smem_bytes(bool f32) {
+  const size_t seg_bytes = (size_t)kSeg * (f32 ? 4 : 8);
+  const size_t map = (size_t)(kFusedMaxCtas + 1) * 16 + (size_t)kCoarseMax * 16 + (size_t)kFWarps * kSeg * 8 +
+                     (size_t)kFWarps * 32 * 16 + (size_t)kFWarps * seg_bytes;
+  const size_t ring = (size_t)kStages * kStageBytes;
+  return map > ring ? map : ring;
 }
 
 template <typename T, bool kVec>
 static cudaError_t fused_t(const FusedLaunch& L, cudaStream_t st) {
-  const int max_b = 2 * num_sms();
-  const size_t smem = (size_t)kMapWarps * kSeg * sizeof(unsigned long long) + (size_t)kMapWarps * 32 * sizeof(u128) +
-                      (size_t)(kMaxCtas + 1) * sizeof(u128) + (size_t)kCoarseMax * sizeof(u128) +
-                      (size_t)kCoarseMax * sizeof(short) + (size_t)kMapWarps * kSeg * sizeof(T);
+  const size_t smem = fused_smem_bytes(sizeof(T) == 4);
   cudaError_t e = cudaFuncSetAttribute(k_fused<T, kVec>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<T, kVec>, kFThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-  if (per_sm > 2) per_sm = 2;
-  const int blocks = num_sms() * per_sm;
-  if (blocks > L.max_blocks || blocks > max_b || blocks > kMaxCtas) return cudaErrorCooperativeLaunchTooLarge;
+  const int blocks = num_sms();
+  if (blocks > kFusedMaxCtas) return cudaErrorCooperativeLaunchTooLarge;
   FusedArgs a;
   a.w = L.w;
   a.M = L.M;
   a.nseg = (L.M + kSeg - 1) / kSeg;
+  a.nfull = L.M / kSeg;
   a.N = L.N;
   a.ndraw = L.N + 1;
-  a.utiles = (a.ndraw + kUTile - 1) / kUTile;
   a.seed = L.seed;
   a.inst = L.inst;
   a.seg = L.seg;
-  a.emax_g = L.emax_g;
-  a.agg = static_cast<u128*>(L.agg);
   a.rel = L.rel;
   a.crel = static_cast<SegPre*>(L.crel);
-  // coarse blocks: at most kCoarseMax, and at most 8 per CTA
-  const long long cmax = kCoarseMax < 8LL * blocks ? kCoarseMax : 8LL * blocks;
-  a.stride = 32;
+  // coarse blocks of 2^lgstride segments, at most kCoarseMax of them
   a.lgstride = 5;
-  while ((a.nseg + a.stride - 1) / a.stride > cmax) {
-    a.stride *= 2;
-    ++a.lgstride;
-  }
-  a.ncoarse = (a.nseg + a.stride - 1) / a.stride;
-  a.consts = L.consts;
+  while (((a.nseg + (1LL << a.lgstride) - 1) >> a.lgstride) > kCoarseMax) ++a.lgstride;
+  a.ncoarse = (a.nseg + (1LL << a.lgstride) - 1) >> a.lgstride;
   a.Z = static_cast<u128*>(L.Z);
-  a.Ztot = static_cast<u128*>(L.Ztot);
-  a.udesc = static_cast<TileDesc<u128>*>(L.udesc);
-  a.work = L.work;
-  a.bar = L.bar;
+  a.xch = L.xch;
   a.status = L.status;
   a.spin = L.spin;
   a.withhold_first = L.withhold_first;
   a.tab = L.tab;
-  long long G = (L.N + (long long)blocks * kFWarps - 1) / ((long long)blocks * kFWarps);
-  a.G = (int)(G < 1 ? 1 : G);
   a.kBS = sizeof(T) == 4 ? FixedTraits<float>::kBias + FixedTraits<float>::kShift
                          : FixedTraits<double>::kBias + FixedTraits<double>::kShift;
   a.out = L.out;

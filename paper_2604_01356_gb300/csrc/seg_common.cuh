@@ -192,8 +192,25 @@ __device__ __forceinline__ uint64_t philox_word(unsigned long long seed, unsigne
   const unsigned q = (unsigned)(k & 3);
   return q == 0 ? words[0] : q == 1 ? words[1] : q == 2 ? words[2] : words[3];
 }
-// 1 / Z_{N+1}.
-__device__ __forceinline__ xf recip_total(u128 t) { return xf_div(xf_from_u64(1, 0), xf_make(t.hi, t.lo, 0)); }
+// Product of two xf, out of line: one copy of the 128x128-bit multiply for
+// the scalar (once per call) paths.
+static __device__ __noinline__ xf xf_mul_ool(xf a, xf b) { return xf_mul(a, b); }
+// 1 / Z_{N+1} (Z_{N+1} > 0): a binary64 estimate of the reciprocal of the
+// top 64 mantissa bits (relative error below 2^-51), then two Newton steps
+// r <- r (2 - m r) on the 128-bit mantissa, each squaring the relative error
+// (2^-51 -> 2^-102 -> the 2^-124 truncation floor of the products).  Integer
+// work only, apart from the one estimate.
+static __device__ __noinline__ xf recip_total(u128 t) {
+  const xf m = xf_make(t.hi, t.lo, 0);  // t = (hi:lo) 2^e, top mantissa bit at 125
+  const unsigned long long top = (m.hi << 2) | (m.lo >> 62);
+  const double y = 1.0 / __ull2double_rn(top);  // ~ 2^-(62 + e) / m
+  xf r = xf_from_f64_bits((uint64_t)__double_as_longlong(y));
+  r.e -= 62 + m.e;
+  const xf two = xf_from_u64(2, 0);
+#pragma unroll 1
+  for (int k = 0; k < 2; ++k) r = xf_mul_ool(r, xf_sub(two, xf_mul_ool(m, r)));
+  return r;
+}
 
 // ---- one tile of the spacing scan ------------------------------------------
 // 256 threads x 4 draws (one Philox block per thread): spacings on the 2^-88
