@@ -103,9 +103,9 @@ cudaError_t launch_w_write(bool f32, bool vec, const void* w, long long M, const
 
 // --- fused single-instance path (one cooperative launch) ----------------
 // Exchange area of the fused kernel (owned by the handle, zeroed once): an
-// epoch word, then two slots of 32 bytes per CTA.
+// epoch word, then two slots of one 128-byte line per CTA.
 constexpr int kFusedMaxCtas = 256;
-constexpr int kFusedXchBytes = 256 + 2 * kFusedMaxCtas * 32;
+constexpr int kFusedXchBytes = 256 + 2 * kFusedMaxCtas * 128;
 struct LogTab;
 struct FusedLaunch {
   const void* w;

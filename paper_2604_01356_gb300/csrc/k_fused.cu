@@ -90,7 +90,9 @@ struct FusedArgs {
 // 64-bit accesses are single-copy atomic, so a reader that sees the tag in all
 // three words has the whole value in one round trip, without a flag.
 constexpr int kLocalSegs = 1024;  // segment records a CTA keeps in shared memory
-static_assert(kFusedMaxCtas * 2 * 32 + 256 <= kFusedXchBytes, "exchange area");
+constexpr int kXSlotWords = 16;   // one 128-byte line per slot
+static_assert(kFusedMaxCtas * 2 * kXSlotWords * 8 + 256 <= kFusedXchBytes, "exchange area");
+static_assert(kFusedMaxCtas <= kFThreads - 32, "the last warp reads no exchange slot");
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -118,6 +120,9 @@ __device__ __forceinline__ bool xget(const unsigned long long* slot, unsigned ta
     a2 = ld_relaxed_u64(slot + 2);
     if ((a0 & 0xFFFFu) == tag && (a1 & 0xFFFFu) == tag && (a2 & 0xFFFFu) == tag) break;
     if (++spins > spin) return false;
+    // every CTA polls every slot: back off so that the slot's own store is
+    // not queued behind the polls
+    __nanosleep(128);
   }
   a0 >>= 16;
   a1 >>= 16;
@@ -128,6 +133,9 @@ __device__ __forceinline__ bool xget(const unsigned long long* slot, unsigned ta
   return true;
 }
 
+// Release / acquire fence at GPU scope (lighter than the sequentially
+// consistent __threadfence).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void st_release_flag(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -158,11 +166,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
   }
   return false;
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
+// Bulk copy global -> shared completing on an mbarrier; the weights stream
+// through L2 with evict-first priority (they are read once), so the segment
+// records, prefixes and code of the later phases stay cached.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                         unsigned long long policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
 }
 
 // One spacing -log v on the 2^-88 grid, out of line (one copy for the four
@@ -177,8 +190,59 @@ __device__ __forceinline__ int seg_owner(long long t, long long nseg, int B) {
   return (int)(((unsigned long long)(t + 1) * (unsigned)B - 1ULL) / (unsigned long long)nseg);
 }
 
+// Polls the slots of CTAs c_lo .. c_lo + n - 1 (n <= kXPerLane) together:
+// every poll issues all outstanding loads at once.
+constexpr int kXPerLane = kFusedMaxCtas / 32;
+__device__ __forceinline__ bool xget_many(const unsigned long long* base, int c_lo, int n, unsigned tag, int spin,
+                                          u128 (&val)[kXPerLane], unsigned (&ext)[kXPerLane]) {
+  unsigned pending = n > 0 ? (1u << n) - 1u : 0u;
+  int spins = 0;
+  while (pending) {
+    unsigned long long a0[kXPerLane], a1[kXPerLane], a2[kXPerLane];
+#pragma unroll
+    for (int k = 0; k < kXPerLane; ++k)
+      if ((pending >> k) & 1u) {
+        const unsigned long long* slot = base + kXSlotWords * (c_lo + k);
+        a0[k] = ld_relaxed_u64(slot);
+        a1[k] = ld_relaxed_u64(slot + 1);
+        a2[k] = ld_relaxed_u64(slot + 2);
+      }
+#pragma unroll
+    for (int k = 0; k < kXPerLane; ++k)
+      if (((pending >> k) & 1u) && (a0[k] & 0xFFFFu) == tag && (a1[k] & 0xFFFFu) == tag &&
+          (a2[k] & 0xFFFFu) == tag) {
+        const unsigned long long p0 = a0[k] >> 16, p1 = a1[k] >> 16, p2 = a2[k] >> 16;
+        val[k].lo = p0 | (p1 << 48);
+        val[k].hi = (p1 >> 16) | ((p2 & 0xFFFFFFFFULL) << 32);
+        ext[k] = (unsigned)(p2 >> 32);
+        pending &= ~(1u << k);
+      }
+    if (!pending) break;
+    if (++spins > spin) {
+#pragma unroll
+      for (int k = 0; k < kXPerLane; ++k)
+        if ((pending >> k) & 1u) {
+          val[k] = u128{0ULL, 0ULL};
+          ext[k] = 0;
+        }
+      return false;
+    }
+    __nanosleep(128);
+  }
+  return true;
+}
+// Warp-wide sum of a u128.
+__device__ __forceinline__ u128 warp_sum_v(u128 v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = u128_add(v, shfl_v(v, (threadIdx.x & 31) ^ o));
+  return v;
+}
+
 // Block-wide exclusive prefix of v (over lower thread indices) and total.
-static __device__ __noinline__ void block_scan(u128 v, u128* s_w, u128& excl, u128& tot) {
+struct BlockScan {
+  u128 excl, tot;
+};
+static __device__ __noinline__ BlockScan block_scan(u128 v, u128* s_w) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u128 incl = warp_incl_scan_v(v, lane);
   if (lane == 31) s_w[warp] = incl;
@@ -190,9 +254,8 @@ static __device__ __noinline__ void block_scan(u128 v, u128* s_w, u128& excl, u1
     if (i < warp) before = u128_add(before, x);
     t = u128_add(t, x);
   }
-  excl = u128_add(before, u128_sub(incl, v));
-  tot = t;
   __syncthreads();  // s_w may be reused
+  return BlockScan{u128_add(before, u128_sub(incl, v)), t};
 }
 
 // ---- the in-segment step of the map, kept small ----------------------------
@@ -467,13 +530,15 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   __shared__ u128 s_S, s_zoff;
   __shared__ int s_Emax;
   __shared__ unsigned s_target;
+  __shared__ u128 s_ztot;
+  __shared__ int s_flag_z, s_flag_inv;  // warp 0 -> last warp: Z_{N+1} ready; back: 1 / Z_{N+1} ready
   __shared__ unsigned long long s_lF[kLocalSegs];  // the CTA's segment records, when they fit
   __shared__ int s_lE[kLocalSegs];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int B = gridDim.x, cta = blockIdx.x;
   const T* w = static_cast<const T*>(a.w);
   unsigned long long* x1 = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(a.xch) + 256);
-  unsigned long long* x2 = x1 + 4 * kFusedMaxCtas;
+  unsigned long long* x2 = x1 + kXSlotWords * kFusedMaxCtas;
 
   // ranges of this CTA
   const long long s0 = a.nseg * cta / B, s1 = a.nseg * (cta + 1) / B;
@@ -483,6 +548,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   const bool local = s1 - s0 <= kLocalSegs;
 
   if (tid == 0) {
+    s_flag_z = 0;
+    s_flag_inv = 0;
     s_target = __ldcg(a.xch) + 1u;  // this call's epoch
     if (kVec) {
       for (int s = 0; s < kStages; ++s) {
@@ -502,6 +569,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   const unsigned tag = target % 65535u + 1u;  // never 0 (a slot never written), differs between calls
   GBR_STAMP(0);
 
+  unsigned long long pol = 0;
+  if (kVec) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
   // stage it of the ring: segments [s0 + it*kStageSegs, ...) of the CTA range
   auto issue = [&](long long it) {
     const int st = (int)(it % kStages);
@@ -509,7 +578,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     const long long sb = sa + kStageSegs < tma_end ? sa + kStageSegs : tma_end;
     const unsigned bytes = (unsigned)((sb - sa) * kSegBytes);
     mbar_expect_tx(&s_full[st], bytes);
-    bulk_g2s(s_dyn + (size_t)st * kStageBytes, w + sa * kSeg, bytes, &s_full[st]);  // one copy per stage
+    bulk_g2s(s_dyn + (size_t)st * kStageBytes, w + sa * kSeg, bytes, &s_full[st], pol);  // one copy per stage
   };
   if (kVec && tid == 0)
     for (long long it = 0; it < n_it && it < kStages; ++it) issue(it);
@@ -543,9 +612,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) pre[q] = run;
       }
-      u128 excl, tot;
-      block_scan(run, s_w, excl, tot);
-      excl = u128_add(excl, ztot);
+      const BlockScan bs = block_scan(run, s_w);
+      const u128 excl = u128_add(bs.excl, ztot), tot = bs.tot;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long k = k0 + q;
@@ -641,13 +709,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     int m = 0;
 #pragma unroll
     for (int i = 0; i < kFWarps; ++i) m = max(m, s_e[i]);
-    if (!(a.withhold_first && cta == 0)) xput(x1 + 4 * cta, tag, ztot, (unsigned)m);
+    if (!(a.withhold_first && cta == 0)) xput(x1 + kXSlotWords * cta, tag, ztot, (unsigned)m);
     GBR_STAMP(25);
   }
   {
     unsigned e = 0;
     u128 z = {0ULL, 0ULL};
-    if (tid < B && !xget(x1 + 4 * tid, tag, a.spin, z, e)) {
+    if (tid < B && !xget(x1 + kXSlotWords * tid, tag, a.spin, z, e)) {
       raise_status(a.status, ST_ETIMEOUT);
       e = 0;
       z = u128{0ULL, 0ULL};
@@ -656,9 +724,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     const int wm = (int)__reduce_max_sync(0xFFFFFFFFu, e);
     GBR_STAMP(8);
     if (lane == 0) s_x[warp] = wm;
-    u128 excl, tot;
-    block_scan(z, s_w, excl, tot);  // (its __syncthreads also publishes s_x)
-    if (tid == cta) s_zoff = excl;  // spacing totals of the CTAs before this one
+    const BlockScan bs = block_scan(z, s_w);  // (its __syncthreads also publishes s_x)
+    const u128 tot = bs.tot;
+    if (tid == cta) s_zoff = bs.excl;  // spacing totals of the CTAs before this one
     if (tid == 0) {
       int m = 0;
 #pragma unroll
@@ -684,8 +752,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
       tsum = u128_add(tsum, grid_value(F, E, Emax));
     }
     GBR_STAMP(20);
-    u128 R, ctot;
-    block_scan(tsum, s_w, R, ctot);
+    const BlockScan bs = block_scan(tsum, s_w);
+    u128 R = bs.excl;
+    const u128 ctot = bs.tot;
     GBR_STAMP(21);
 #pragma unroll 1
     for (long long s = t_lo; s < t_hi; ++s) {
@@ -698,14 +767,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     __syncthreads();  // rel, crel and the segment records precede the published total
     GBR_STAMP(22);
     if (tid == 0) {
-      __threadfence();
+      fence_acq_rel_gpu();  // release: rel, crel and the segment records precede the total
       GBR_STAMP(23);
-      xput(x2 + 4 * cta, tag, ctot, 0u);
+      xput(x2 + kXSlotWords * cta, tag, ctot, 0u);
       GBR_STAMP(15);
-      // 1 / Z_{N+1} while the other CTAs finish
+    }
+    if (tid == kFThreads - 32) {
+      // 1 / Z_{N+1} while the exchange completes (this thread reads no slot)
       const u128 zt = s_S;
       s_invZ = u128_is_zero(zt) ? lb_zero<xf>() : recip_total(zt);
-      GBR_STAMP(9);
+      GBR_STAMP_IF(true, 9);
     }
   }
   GBR_STAMP(4);
@@ -728,18 +799,18 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     unsigned e = 0;
     u128 v = {0ULL, 0ULL};
     if (tid < B) {
-      if (!xget(x2 + 4 * tid, tag, a.spin, v, e)) {
+      if (!xget(x2 + kXSlotWords * tid, tag, a.spin, v, e)) {
         raise_status(a.status, ST_ETIMEOUT);
         v = u128{0ULL, 0ULL};
       }
       GBR_STAMP(16);
-      __threadfence();  // acquire: the publishers' segment data are read below
+      fence_acq_rel_gpu();  // acquire: the publishers' segment data are read below
       GBR_STAMP(17);
     }
-    u128 excl, tot;
-    block_scan(v, s_w, excl, tot);
+    const BlockScan bs = block_scan(v, s_w);
+    const u128 tot = bs.tot;
     GBR_STAMP(18);
-    if (tid < B) s_cp[tid] = excl;
+    if (tid < B) s_cp[tid] = bs.excl;
     if (tid == 0) {
       s_cp[B] = tot;
       s_S = tot;
