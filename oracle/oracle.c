@@ -293,18 +293,44 @@ int64_t orc_alg5_dac_map(const double* W, int64_t M, const double* U, int64_t N,
  * w_is_f32 selects binary32 weights; single selects binary32 draws (the
  * compensated-binary32 path's stream), both evaluated here in binary64.
  * W_out, U_out may be NULL.  Returns the orc_cumulative status. */
-int orc_resample(const void* w, int w_is_f32, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
-                 int single, int32_t* r, double* W_out, double* U_out) {
+/* Stratified and systematic uniforms, the variants the paper's concluding
+ * section says the method extends to: N points, one per stratum
+ * ((i-1)/N, i/N], i = 1..N, with the same draws v_k as Algorithm 1:
+ *   stratified  U_i = (i - 1 + v_{i-1}) / N   (a fresh draw per stratum)
+ *   systematic  U_i = (i - 1 + v_0) / N       (one draw for all strata)
+ * scheme 0 is Algorithm 1 itself. */
+void orc_scheme_uniform(uint64_t seed, uint64_t instance, int64_t N, int single, int scheme, double* U) {
+  if (N <= 0) return;
+  if (scheme == 0) {
+    orc_sorted_uniform(seed, instance, N, single, U);
+    return;
+  }
+  const double v0 = orc_uniform_from_word(orc_stream_word(seed, instance, 0), single);
+  for (int64_t i = 0; i < N; ++i) {
+    const double v = scheme == 1 ? orc_uniform_from_word(orc_stream_word(seed, instance, (uint64_t)i), single) : v0;
+    U[i] = ((double)i + v) / (double)N;
+  }
+}
+
+/* Whole path with the uniforms of `scheme` (0: Algorithm 1, 1: stratified,
+ * 2: systematic). */
+int orc_resample_scheme(const void* w, int w_is_f32, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                        int single, int scheme, int32_t* r, double* W_out, double* U_out) {
   double* W = W_out ? W_out : (double*)malloc((size_t)M * sizeof(double));
   double* U = U_out ? U_out : (double*)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
   int rc = w_is_f32 ? orc_cumulative_f32((const float*)w, M, W, NULL) : orc_cumulative((const double*)w, M, W, NULL);
   if (rc == 0 && N > 0) {
-    orc_sorted_uniform(seed, instance, N, single, U);
+    orc_scheme_uniform(seed, instance, N, single, scheme, U);
     orc_inverse_cdf_walk(W, M, U, N, r);
   }
   if (!W_out) free(W);
   if (!U_out) free(U);
   return rc;
+}
+
+int orc_resample(const void* w, int w_is_f32, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                 int single, int32_t* r, double* W_out, double* U_out) {
+  return orc_resample_scheme(w, w_is_f32, M, N, seed, instance, single, 0, r, W_out, U_out);
 }
 
 /* K instances laid out back to back: instance k owns w[woff[k] .. woff[k+1])

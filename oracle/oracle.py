@@ -56,6 +56,10 @@ def lib():
         L.orc_alg5_dac_map.restype = _i64
         L.orc_resample.argtypes = [_p, _int, _i64, _i64, _u64, _u64, _int, _p, _p, _p]
         L.orc_resample.restype = _int
+        L.orc_scheme_uniform.argtypes = [_u64, _u64, _i64, _int, _int, _p]
+        L.orc_scheme_uniform.restype = None
+        L.orc_resample_scheme.argtypes = [_p, _int, _i64, _i64, _u64, _u64, _int, _int, _p, _p, _p]
+        L.orc_resample_scheme.restype = _int
         L.orc_resample_batched.argtypes = [_p, _int, _p, _p, _i64, _u64, _int, _p]
         L.orc_resample_batched.restype = _int
         _lib = L
@@ -100,6 +104,18 @@ def sorted_uniform(N, seed, instance=0, single=False):
     """Algorithm 1 with normaliser Z_{N+1}: N sorted uniforms in (0,1]."""
     U = np.zeros(max(N, 1), dtype=np.float64)
     lib().orc_sorted_uniform(seed, instance, N, int(bool(single)), _ptr(U))
+    return U[:N]
+
+
+SCHEMES = {"multinomial": 0, "stratified": 1, "systematic": 2}
+
+
+def scheme_uniform(N, seed, instance=0, scheme="stratified", single=False):
+    """N uniforms of a scheme: Algorithm 1 ('multinomial'), or one point per
+    stratum ((i-1)/N, i/N]: U_i = (i-1+v_{i-1})/N ('stratified') or
+    (i-1+v_0)/N ('systematic'), with Algorithm 1's draws v_k."""
+    U = np.zeros(max(N, 1), dtype=np.float64)
+    lib().orc_scheme_uniform(seed, instance, N, int(bool(single)), SCHEMES[scheme], _ptr(U))
     return U[:N]
 
 
@@ -191,6 +207,21 @@ def resample(w, N, seed, instance=0, single=False):
     W = np.zeros(max(M, 1), dtype=np.float64)
     U = np.zeros(max(N, 1), dtype=np.float64)
     rc = lib().orc_resample(_ptr(ww), int(is32), M, N, seed, instance, int(bool(single)), _ptr(r), _ptr(W), _ptr(U))
+    if rc:
+        raise OracleError(rc)
+    return r[:N], W[:M], U[:N]
+
+
+def resample_scheme(w, N, seed, scheme, instance=0, single=False):
+    """Whole path with the uniforms of `scheme`: (r, W, U)."""
+    is32 = w.dtype == np.float32
+    ww = np.ascontiguousarray(w) if is32 else _f64(w)
+    M = ww.shape[0]
+    r = np.zeros(max(N, 1), dtype=np.int32)
+    W = np.zeros(max(M, 1), dtype=np.float64)
+    U = np.zeros(max(N, 1), dtype=np.float64)
+    rc = lib().orc_resample_scheme(_ptr(ww), int(is32), M, N, seed, instance, int(bool(single)), SCHEMES[scheme],
+                                   _ptr(r), _ptr(W), _ptr(U))
     if rc:
         raise OracleError(rc)
     return r[:N], W[:M], U[:N]

@@ -301,3 +301,70 @@ def test_resample_batched_equals_instance_loop():
     for k in range(6):
         rk, _, _ = oracle.resample(w[woff[k]:woff[k + 1]], int(roff[k + 1] - roff[k]), seed=21, instance=k, single=True)
         assert np.array_equal(r[roff[k]:roff[k + 1]], rk)
+
+
+# ---------------------------------------------- stratified / systematic ----
+# The variants the paper's concluding section names: one point per stratum
+# ((i-1)/N, i/N], with the draws of Algorithm 1.
+
+@pytest.mark.parametrize("scheme", ["stratified", "systematic"])
+@pytest.mark.parametrize("N", [1, 2, 7, 1000, 4097])
+def test_scheme_one_point_per_stratum(scheme, N):
+    U = oracle.scheme_uniform(N, 11, 3, scheme)
+    i = np.arange(N, dtype=np.float64)
+    assert np.all(U >= i / N) and np.all(U <= (i + 1) / N)
+    assert np.all(np.diff(U) >= 0) and U[-1] <= 1.0 and U[0] > 0
+
+
+def test_systematic_points_equally_spaced():
+    N = 1000
+    U = oracle.scheme_uniform(N, 4, 0, "systematic")
+    assert np.allclose(np.diff(U), 1.0 / N, rtol=0, atol=1e-15)
+
+
+def test_stratified_strata_are_independent_draws():
+    # the position inside each stratum, N U_i - (i-1), is Uniform(0,1): KS
+    from scipy import stats
+    N = 20000
+    U = oracle.scheme_uniform(N, 8, 1, "stratified")
+    frac = N * U - np.arange(N)
+    assert stats.kstest(frac, "uniform").pvalue > 1e-3
+
+
+def _counts(r, M):
+    return np.bincount(r, minlength=M)
+
+
+def test_systematic_counts_are_floor_or_ceil():
+    # N equally spaced points: an interval of W of length w_j holds
+    # floor(N w_j) or ceil(N w_j) of them
+    rng = np.random.default_rng(5)
+    for M, N in [(50, 40), (1000, 5000), (3000, 700)]:
+        w = rng.exponential(size=M)
+        r, W, _ = oracle.resample_scheme(w, N, 17, "systematic")
+        e = N * w / w.sum()
+        c = _counts(r, M)
+        assert np.all(c >= np.floor(e - 1e-9)) and np.all(c <= np.ceil(e + 1e-9))
+
+
+def test_stratified_counts_within_one_and_unbiased():
+    rng = np.random.default_rng(6)
+    M, N = 40, 100
+    w = rng.exponential(size=M)
+    e = N * w / w.sum()
+    mean = np.zeros(M)
+    seeds = 400
+    for seed in range(seeds):
+        r, _, _ = oracle.resample_scheme(w, N, seed, "stratified")
+        c = _counts(r, M)
+        # an interval of length w_j meets at most ceil(N w_j) + 1 strata
+        assert np.all(c >= np.floor(e) - 1) and np.all(c <= np.ceil(e) + 1)
+        mean += c
+    mean /= seeds
+    # each stratum's point falls in j with its probability: E[count_j] = N w_j
+    assert np.all(np.abs(mean - e) <= 4 * np.sqrt(np.maximum(e, 0.25) / seeds) + 1e-9)
+
+
+def test_scheme_zero_is_algorithm_1():
+    U0 = oracle.scheme_uniform(333, 9, 2, "multinomial")
+    assert np.array_equal(U0, oracle.sorted_uniform(333, 9, 2))
