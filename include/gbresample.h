@@ -75,6 +75,17 @@ typedef enum {
  *              for the final normalisation; W within 4*2^-23 of exact. */
 typedef enum { RS_F64 = 0, RS_F32_COMP = 1 } rs_precision;
 
+/* The N points U_1 <= ... <= U_N fed to the inverse CDF (Eq. 2).
+ *  RS_SCHEME_MULTINOMIAL  Alg. 1: the order statistics of N uniforms
+ *                         (N+1 draws, exponential spacings); the paper's method.
+ *  RS_SCHEME_STRATIFIED   one point per stratum ((i-1)/N, i/N]:
+ *                         U_i = (i - 1 + v_{i-1}) / N, draws v_0 .. v_{N-1}.
+ *  RS_SCHEME_SYSTEMATIC   U_i = (i - 1 + v_0) / N, one draw.
+ * The last two are the variants the paper's concluding section says the
+ * method extends to; only the points change, the map is the same.  The draws
+ * v_k are those of Alg. 1 (same Philox words). */
+typedef enum { RS_SCHEME_MULTINOMIAL = 0, RS_SCHEME_STRATIFIED = 1, RS_SCHEME_SYSTEMATIC = 2 } rs_scheme;
+
 /* Options.  A NULL rs_opts pointer, or a zeroed struct, selects defaults. */
 typedef struct {
   int32_t algo;        /* rs_map_algo (default RS_MAP_DAC) */
@@ -95,7 +106,7 @@ typedef struct {
                           launch (identical results; for comparison). */
   int32_t tile_threads; /* rs_resample_batched: threads per CTA, 128, 256 or 512
                            (0 = the autotuned or default value); ignored elsewhere */
-  int32_t reserved;    /* must be zero */
+  int32_t scheme;      /* rs_scheme of the N uniforms (default RS_SCHEME_MULTINOMIAL) */
 } rs_opts;
 
 /* Create a handle bound to the CUDA device current on the calling thread.

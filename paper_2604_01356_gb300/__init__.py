@@ -9,6 +9,7 @@ CPU path, and importing fails loudly when the library is missing.
 from ._binding import (  # noqa: F401
     RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_EZEROSUM, RS_ETIMEOUT, RS_ECAPACITY, RS_OK, RS_STATIC_MAX_N,
     RS_F32_COMP, RS_F64, RS_MAP_BINARY, RS_MAP_DAC, RS_MAP_LINEAR,
+    RS_SCHEME_MULTINOMIAL, RS_SCHEME_STRATIFIED, RS_SCHEME_SYSTEMATIC,
     ResampleError, Handle, lib, library_path, opts,
     rs_create, rs_destroy, rs_get_status, rs_last_error, rs_version,
     rs_resample_w, rs_resample_W, rs_sorted_uniform, rs_sorted_uniform_static, rs_cumulative, rs_map, rs_philox,

@@ -9,6 +9,7 @@ RS_OK, RS_EINVAL, RS_ENOMEM, RS_ECUDA, RS_ENONFINITE, RS_EZEROSUM, RS_ETIMEOUT, 
 RS_STATIC_MAX_N = 65536
 RS_MAP_DAC, RS_MAP_BINARY, RS_MAP_LINEAR = 0, 1, 2
 RS_F64, RS_F32_COMP = 0, 1
+RS_SCHEME_MULTINOMIAL, RS_SCHEME_STRATIFIED, RS_SCHEME_SYSTEMATIC = 0, 1, 2
 _NAMES = {0: "RS_OK", 1: "RS_EINVAL", 2: "RS_ENOMEM", 3: "RS_ECUDA", 4: "RS_ENONFINITE", 5: "RS_EZEROSUM",
           6: "RS_ETIMEOUT", 7: "RS_ECAPACITY"}
 
@@ -22,11 +23,12 @@ class ResampleError(RuntimeError):
 class rs_opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("prec", ctypes.c_int32), ("leaf_L", ctypes.c_int32),
                 ("stage_max", ctypes.c_int32), ("spin_limit", ctypes.c_int32), ("debug_flags", ctypes.c_int32),
-                ("tile_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tile_threads", ctypes.c_int32), ("scheme", ctypes.c_int32)]
 
 
-def opts(algo=RS_MAP_DAC, prec=RS_F64, leaf_L=0, stage_max=0, spin_limit=0, debug_flags=0, tile_threads=0):
-    return rs_opts(algo, prec, leaf_L, stage_max, spin_limit, debug_flags, tile_threads)
+def opts(algo=RS_MAP_DAC, prec=RS_F64, leaf_L=0, stage_max=0, spin_limit=0, debug_flags=0, tile_threads=0,
+         scheme=RS_SCHEME_MULTINOMIAL):
+    return rs_opts(algo, prec, leaf_L, stage_max, spin_limit, debug_flags, tile_threads, scheme)
 
 
 _lib = None

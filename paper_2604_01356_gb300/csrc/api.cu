@@ -119,6 +119,7 @@ struct Opts {
   int spin = kDefaultSpin;
   int debug = 0;
   int threads = 0;
+  int scheme = RS_SCHEME_MULTINOMIAL;
 };
 
 rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec) {
@@ -131,7 +132,9 @@ rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec)
       return fail(h, RS_EINVAL, "opts.leaf_L must be 0 or a power of two <= 1024");
     if (o->stage_max < 0) return fail(h, RS_EINVAL, "opts.stage_max negative");
     if (o->spin_limit < 0) return fail(h, RS_EINVAL, "opts.spin_limit negative");
-    if (o->reserved) return fail(h, RS_EINVAL, "opts.reserved must be zero");
+    if (o->scheme < RS_SCHEME_MULTINOMIAL || o->scheme > RS_SCHEME_SYSTEMATIC)
+      return fail(h, RS_EINVAL, "opts.scheme must be RS_SCHEME_MULTINOMIAL, _STRATIFIED or _SYSTEMATIC");
+    r.scheme = o->scheme;
     if (o->tile_threads != 0 && o->tile_threads != 128 && o->tile_threads != 256 && o->tile_threads != 512)
       return fail(h, RS_EINVAL, "opts.tile_threads must be 0, 128, 256 or 512");
     r.threads = o->tile_threads;
@@ -308,7 +311,7 @@ rs_status enqueue_uniforms(rs_handle* h, const Plan& p, bool f32, uint64_t seed,
     RS_TRACE(h, "uniform_scan", st);
     RS_CK(h, launch_uniform_scan(f32, p.ndraw, seed, inst, at<void>(h, p.o_Z), at<void>(h, p.o_Ztot),
                                  at<PathConsts>(h, p.o_consts), at<void>(h, p.o_udesc), ctr_u(h, p), h->status,
-                                 o.spin, o.debug & 1, st));
+                                 o.spin, o.debug & 1, st, o.scheme));
   }
   if (U_out) {
     RS_TRACE(h, "uniform_norm", st);
@@ -585,6 +588,7 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
     F.withhold_first = o.debug & 1;
     F.tab = static_cast<const LogTab*>(h->logtab);
     F.out = out_idx;
+    F.scheme = o.scheme;
     cudaError_t e;
     {
       RS_TRACE(h, "fused", st);
@@ -691,6 +695,7 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
   memset(&one, 0, sizeof(one));
   one.prec = o.prec;
   one.spin_limit = o.spin;
+  one.scheme = o.scheme;
   // instances the persistent kernel does not take: every one in binary64,
   // the large ones in binary32
   for (int32_t k = 0; k < K; ++k) {
@@ -716,7 +721,7 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
     RS_TRACE(h, "batched", st);
     RS_CK(h, launch_batched_f32(static_cast<const float*>(w), reinterpret_cast<const long long*>(w_off),
                                 reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, threads, leaf,
-                                out_idx, at<unsigned>(h, o_queue), h->status, st));
+                                out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme));
   }
   return RS_OK;
 }
@@ -734,6 +739,7 @@ rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off,
   rs_opts c;
   memset(&c, 0, sizeof(c));
   c.prec = o.prec;
+  c.scheme = o.scheme;
   c.spin_limit = opts ? opts->spin_limit : 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   RS_CK(h, cudaEventCreate(&e0));

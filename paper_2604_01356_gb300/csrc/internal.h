@@ -82,9 +82,10 @@ void fill_log_table(LogTab& h);  // host copy of the logarithm table
 size_t log_table_bytes();
 cudaError_t upload_log_table(void* dst);  // synchronous copy into device memory
 struct PathConsts;
+// scheme: 0 Algorithm 1 (sorted uniforms), 1 stratified, 2 systematic points.
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst,
                                 void* Z, void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
-                                int spin_limit, bool withhold_first, cudaStream_t st);
+                                int spin_limit, bool withhold_first, cudaStream_t st, int scheme = 0);
 cudaError_t launch_uniform_norm(long long N, const void* Z, const PathConsts* consts, double* U, cudaStream_t st);
 cudaError_t launch_philox(unsigned long long seed, unsigned long long inst, unsigned long long first, long long n,
                           unsigned long long* out, cudaStream_t st);
@@ -121,6 +122,7 @@ struct FusedLaunch {
   bool withhold_first;
   const LogTab* tab;  // device copy of the logarithm table
   int* out;
+  int scheme;        // uniforms: 0 Algorithm 1, 1 stratified, 2 systematic
 };
 // Returns cudaErrorCooperativeLaunchTooLarge (nothing launched) when the
 // device cannot hold the whole grid at once.
@@ -136,7 +138,7 @@ constexpr int kSortMax = 16384;   // batches up to this size are ordered by M_k 
 cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cudaStream_t st);
 cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                                unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st);
+                               int* status, cudaStream_t st, int scheme = 0);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

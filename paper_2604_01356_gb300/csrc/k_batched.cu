@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
                                                           const long long* __restrict__ r_off,
                                                           const int* __restrict__ order, int K,
                                                           unsigned long long seed, int leaf_T,
-                                                          int* __restrict__ out, unsigned* queue, int* status) {
+                                                          int* __restrict__ out, unsigned* queue, int* status,
+                                                          int scheme) {
   using Tr = FixedTraits<float>;
   using Bits = Tr::Bits;
   constexpr int kWarps = kThreads / 32;
@@ -162,15 +163,24 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
     // ---- C: Z_{N+1}, the sum of all N+1 spacings ----------------------------
     const long long ndraw = Nk + 1;
     u128 zsum = {0ULL, 0ULL};
-    for (long long d0 = (long long)tid * 4; d0 < ndraw; d0 += kChunk) {
-      uint64_t wd[4];
-      philox4x64_10((uint64_t)(d0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
+    if (scheme == kSchemeMultinomial)
+      for (long long d0 = (long long)tid * 4; d0 < ndraw; d0 += kChunk) {
+        uint64_t wd[4];
+        philox4x64_10((uint64_t)(d0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (d0 + q < ndraw) zsum = u128_add(zsum, spacing_fixed<true>(wd[q], nullptr));
-    }
+        for (int q = 0; q < 4; ++q)
+          if (d0 + q < ndraw) zsum = u128_add(zsum, spacing_fixed<true>(wd[q], nullptr));
+      }
+    else if (tid == 0)
+      zsum = u128{0ULL, (unsigned long long)Nk << 24};  // the strata spacings telescope to N
     u128 Ztot;
     (void)block_excl_scan<kWarps>(zsum, sm.wsum, Ztot);
+    u128 vsys = {0ULL, 0ULL};  // systematic: the one draw v_0
+    if (scheme == kSchemeSystematic) {
+      uint64_t w0[4];
+      philox4x64_10(0ULL, 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, w0);
+      vsys = draw_fixed<true>(w0[0]);
+    }
     if (tid == 0) compute_c(&sm.c, S, Ztot);
     __syncthreads();
     const xf c = sm.c;
@@ -193,7 +203,24 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
         const int wq = lane & 3;
         const uint64_t word = wq == 0 ? x0 : wq == 1 ? x1 : wq == 2 ? x2 : x3;
         const long long d = wbase + 32 * r + lane;
-        f[r] = d < Nk ? spacing_fixed<true>(word, nullptr) : u128{0ULL, 0ULL};
+        if (scheme == kSchemeMultinomial) {
+          f[r] = d < Nk ? spacing_fixed<true>(word, nullptr) : u128{0ULL, 0ULL};
+        } else {
+          // word d - 1: the previous word of this block, the last word of the
+          // previous lane's block, or (draw 32 r of the chunk) recomputed
+          uint64_t wp = __shfl_sync(0xFFFFFFFFu, wd[3], src > 0 ? src - 1 : 0);
+          if (wq == 1) wp = x0;
+          if (wq == 2) wp = x1;
+          if (wq == 3) wp = x2;
+          if (wq == 0 && src == 0 && d > 0) {
+            uint64_t pw[4];
+            philox4x64_10((uint64_t)(d / 4 - 1), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, pw);
+            wp = pw[3];
+          }
+          const u128 vk = scheme == kSchemeSystematic ? vsys : draw_fixed<true>(word);
+          const u128 vp = scheme == kSchemeSystematic ? vsys : draw_fixed<true>(wp);
+          f[r] = d < Nk ? strata_spacing(d, Nk, vk, vp) : u128{0ULL, 0ULL};
+        }
         inc[r] = warp_incl_scan_v(f[r], lane);
         const u128 t = shfl_v(inc[r], 31);
         inc[r] = u128_add(inc[r], wtot);  // plus the earlier rounds of this warp
@@ -285,7 +312,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
 template <int kThreads>
 static cudaError_t batched_t(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                              unsigned long long seed, int leaf_T, int* out, unsigned* queue, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, int scheme) {
   const size_t smem = sizeof(BatchSmem<kThreads / 32>);
   cudaError_t e = cudaFuncSetAttribute(k_batched_f32<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -297,18 +324,18 @@ static cudaError_t batched_t(const float* w, const long long* w_off, const long 
   if (blocks > K) blocks = K;
   if (blocks < 1) blocks = 1;
   k_batched_f32<kThreads><<<(unsigned)blocks, kThreads, smem, st>>>(w, w_off, r_off, order, K, seed, leaf_T, out,
-                                                                     queue, status);
+                                                                     queue, status, scheme);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                                unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st) {
+                               int* status, cudaStream_t st, int scheme) {
   if (K <= 0) return cudaSuccess;
   switch (threads) {
-    case 128: return batched_t<128>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st);
-    case 512: return batched_t<512>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st);
-    default: return batched_t<256>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st);
+    case 128: return batched_t<128>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
+    case 512: return batched_t<512>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
+    default: return batched_t<256>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
   }
 }
 

@@ -83,6 +83,7 @@ struct FusedArgs {
   const LogTab* tab;  // logarithm table (binary64 draws)
   int kBS;
   int* out;
+  int scheme;         // uniforms: Algorithm 1, stratified or systematic points
 };
 
 // Exchange slots: a published value of up to 144 bits travels in three
@@ -599,13 +600,31 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
       const long long k0 = t0 + 4LL * tid;
       u128 pre[4];
       u128 run = {0ULL, 0ULL};
-      if (k0 < d1 && k0 + 3 >= d0) {
+      const bool mine = k0 < d1 && k0 + 3 >= d0;
+      if (a.scheme == kSchemeMultinomial) {
+        if (mine) {
+          uint64_t words[4];
+          philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const long long k = k0 + q;
+            if (k >= d0 && k < d1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
+            pre[q] = run;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) pre[q] = run;
+        }
+      } else if (__any_sync(0xFFFFFFFFu, mine)) {
+        // strata points: every lane of the warp takes part (neighbour words)
         uint64_t words[4];
         philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
+        u128 f[4];
+        block_spacings<F32>(a.scheme, k0, a.ndraw, a.seed, a.inst, words, &tab, f);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const long long k = k0 + q;
-          if (k >= d0 && k < d1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
+          if (k >= d0 && k < d1) run = u128_add(run, f[q]);
           pre[q] = run;
         }
       } else {
@@ -897,6 +916,7 @@ static cudaError_t fused_t(const FusedLaunch& L, cudaStream_t st) {
   a.kBS = sizeof(T) == 4 ? FixedTraits<float>::kBias + FixedTraits<float>::kShift
                          : FixedTraits<double>::kBias + FixedTraits<double>::kShift;
   a.out = L.out;
+  a.scheme = L.scheme;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kFThreads);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
                                                            unsigned long long inst, u128* __restrict__ Z,
                                                            u128* __restrict__ Ztot, PathConsts* consts,
                                                            TileDesc<u128>* desc, unsigned* ctr, int* status,
-                                                           int spin_limit, bool withhold_first) {
+                                                           int spin_limit, bool withhold_first, int scheme) {
   __shared__ LogTab tab;
   __shared__ UniformTileSmem us;
   __shared__ unsigned s_tile;
@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
   }
   if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
   __syncthreads();
-  uniform_tile<F32>(s_tile, ndraw, seed, inst, Z, Ztot, consts, desc, status, spin_limit, withhold_first, &tab, us);
+  uniform_tile<F32>(s_tile, ndraw, seed, inst, Z, Ztot, consts, desc, status, spin_limit, withhold_first, &tab, us,
+                    scheme);
 }
 
 // U_i = Z_i / Z_{N+1} rounded to binary64: integer multiply by the reciprocal
@@ -92,15 +93,15 @@ cudaError_t upload_log_table(void* dst) {
 
 cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,
                                 void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
-                                int spin_limit, bool withhold_first, cudaStream_t st) {
+                                int spin_limit, bool withhold_first, cudaStream_t st, int scheme) {
   const long long tiles = (ndraw + kUTile - 1) / kUTile;
   if (tiles <= 0) return cudaSuccess;
   if (f32)
     k_uniform_scan<true><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
-                                                                (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first);
+                                                                (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first, scheme);
   else
     k_uniform_scan<false><<<(unsigned)tiles, kUThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, (u128*)Ztot, consts,
-                                                                 (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first);
+                                                                 (TileDesc<u128>*)desc, ctr, status, spin_limit, withhold_first, scheme);
   return cudaGetLastError();
 }
 

@@ -185,6 +185,31 @@ __device__ __forceinline__ u128 spacing_fixed(uint64_t word, const LogTab* tab) 
   const u128 f = f_to_fixed128<kZFrac>(z.hi);
   return (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
 }
+// ---- stratified and systematic points ----------------------------------------
+// Schemes of the uniforms: Algorithm 1's sorted uniforms, or one point per
+// stratum ((i-1)/N, i/N] -- U_i = (i-1+v_{i-1})/N (stratified) or
+// (i-1+v_0)/N (systematic) -- the variants named in the paper's conclusion.
+// The strata points reuse the spacing machinery unchanged: their "spacings"
+//   s_0 = v'_0,  s_k = 1 + v'_k - v'_{k-1} (0 < k < N),  s_N = 1 - v'_{N-1}
+// (v'_k = v_k stratified, v_0 systematic; all on the 2^-88 grid, exact) have
+// the prefix sums Z_i = i - 1 + v'_{i-1} and Z_{N+1} = N, so the keys
+// ceil(Z_i S / Z_{N+1}) are those of the strata points.
+enum : int { kSchemeMultinomial = 0, kSchemeStratified = 1, kSchemeSystematic = 2 };
+// Draw v of Philox word x on the 2^-88 grid (exact): binary64 draws
+// (2 (x >> 12) + 1) 2^-53, binary32 draws (2 (x >> 41) + 1) 2^-24.
+template <bool F32>
+__device__ __forceinline__ u128 draw_fixed(uint64_t x) {
+  if (F32) return u128{0ULL, 2ULL * (x >> 41) + 1ULL};  // (2m+1) 2^64
+  const uint64_t m = 2ULL * (x >> 12) + 1ULL;           // < 2^53
+  return u128{m << 35, m >> 29};                         // (2m+1) 2^35
+}
+__device__ __forceinline__ u128 strata_spacing(long long k, long long N, const u128& vk, const u128& vp) {
+  const u128 one = {0ULL, 1ULL << 24};  // 1 on the 2^-88 grid
+  if (k == 0) return vk;
+  if (k >= N) return u128_sub(one, vp);
+  return u128_sub(u128_add(one, vk), vp);
+}
+
 // Philox word k of the stream (seed, instance).
 __device__ __forceinline__ uint64_t philox_word(unsigned long long seed, unsigned long long inst, long long k) {
   uint64_t words[4];
@@ -237,22 +262,61 @@ static __device__ __noinline__ void store_recip(unsigned long long* dst, u128 t)
   dst[2] = (unsigned long long)r.e;
 }
 
+// The spacings of draws k0 .. k0+3 (one Philox block, words) under a scheme
+// (N = ndraw - 1).  The stratified spacing of draw k also needs word k-1:
+// the previous lane's last word, or the previous block's for lane 0.
+template <bool F32>
+__device__ __forceinline__ void block_spacings(int scheme, long long k0, long long ndraw, unsigned long long seed,
+                                               unsigned long long inst, const uint64_t (&words)[4], const LogTab* tab,
+                                               u128 (&f)[4]) {
+  const long long N = ndraw - 1;
+  if (scheme == kSchemeMultinomial) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = k0 + q < ndraw ? spacing_fixed<F32>(words[q], tab) : u128{0ULL, 0ULL};
+    return;
+  }
+  u128 vprev;
+  if (scheme == kSchemeSystematic) {
+    uint64_t w0[4];
+    philox4x64_10(0ULL, 0ULL, 0ULL, 0ULL, seed, inst, w0);
+    vprev = draw_fixed<F32>(w0[0]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) f[q] = k0 + q < ndraw ? strata_spacing(k0 + q, N, vprev, vprev) : u128{0ULL, 0ULL};
+    return;
+  }
+  uint64_t wp = __shfl_up_sync(0xFFFFFFFFu, words[3], 1);
+  if ((threadIdx.x & 31) == 0 && k0 > 0) {
+    uint64_t pw[4];
+    philox4x64_10((uint64_t)(k0 / 4 - 1), 0ULL, 0ULL, 0ULL, seed, inst, pw);
+    wp = pw[3];
+  }
+  vprev = draw_fixed<F32>(wp);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const u128 vk = draw_fixed<F32>(words[q]);
+    f[q] = k0 + q < ndraw ? strata_spacing(k0 + q, N, vk, vprev) : u128{0ULL, 0ULL};
+    vprev = vk;
+  }
+}
+
 template <bool F32>
 __device__ __forceinline__ void uniform_tile(long long tile, long long ndraw, unsigned long long seed,
                                              unsigned long long inst, u128* __restrict__ Z, u128* __restrict__ Ztot,
                                              PathConsts* consts, TileDesc<u128>* desc, int* status, int spin_limit,
-                                             bool withhold_first, const LogTab* tab, UniformTileSmem& us) {
+                                             bool withhold_first, const LogTab* tab, UniformTileSmem& us,
+                                             int scheme = kSchemeMultinomial) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long k0 = tile * kUTile + (long long)threadIdx.x * kUItems;
   // the thread's four draws are the four words of one Philox block
   uint64_t words[4];
   philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
   u128 pre[kUItems];  // thread-local inclusive prefixes
+  u128 fq[kUItems];
+  block_spacings<F32>(scheme, k0, ndraw, seed, inst, words, tab, fq);
   u128 run = {0ULL, 0ULL};
 #pragma unroll
   for (int q = 0; q < kUItems; ++q) {
-    const u128 f = k0 + q < ndraw ? spacing_fixed<F32>(words[q], tab) : u128{0ULL, 0ULL};
-    run = u128_add(run, f);
+    run = u128_add(run, fq[q]);
     pre[q] = run;
   }
   const u128 incl = warp_incl_scan_v(run, lane);
