@@ -9,7 +9,7 @@ Workload (one step = one pass of the whole path over one instance):
 
 Prints ONE JSON line (rank 0).  `value` is resampled particles/s over all
 ranks (each rank resamples its own instance: weak scaling, no collective on
-the data path).  L2 is flushed (256 MiB write) before every timed step and
+the data path).  L2 is flushed (256 MiB write, read back) before every timed step and
 each step is timed with CUDA events on its stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -35,6 +35,22 @@ METRIC = "resampled particles/s and HBM GB/s vs roofline; batched FP32 vs per-in
 UNIT = "particles/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
+
+
+def make_flush(dev):
+    """An L2 flush: write a 256 MiB buffer (larger than L2), then read it back
+    so that no dirty flush lines remain to be written back inside the timed
+    region.  Returns the function that flushes (outside the timed events)."""
+    import torch
+    buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1, dtype=torch.int64, device=dev)
+    state = {"k": 0}
+
+    def flush():
+        state["k"] += 1
+        buf.fill_(state["k"] & 255)
+        sink.add_(buf.view(torch.int64).sum())
+    return flush
 
 
 def parse():
@@ -220,7 +236,7 @@ def run_ours(args):
     M, N, seed = wl.M, wl.N, wl.seed
     wd = torch.from_numpy(wl.w).to(dev)
     out = torch.empty(N, dtype=torch.int32, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    flush = make_flush(dev)
     h = g.Handle()
     stream = torch.cuda.Stream(device=dev)
     inst = rank_instance(rank)
@@ -230,7 +246,7 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
-            flush.zero_()
+            flush()
             step(stream)
     stream.synchronize()
     if h.status() != g.RS_OK:
@@ -254,7 +270,7 @@ def run_ours(args):
     time.sleep(0.3)
     with torch.cuda.stream(stream):
         for k in range(K):
-            flush.zero_()
+            flush()
             ev[k][0].record(stream)
             graph.replay()
             ev[k][1].record(stream)
@@ -294,7 +310,7 @@ def run_ours(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "engmf: M=16,777,216 binary64 weights exp(l - max l), l~Normal(0,2^2); N=4,096; "
                                "rs_resample_w (Eq.3 + Alg.1 + segmented DaC map) as a CUDA graph",
-                   "M": M, "N": N, "precision": "f64", "l2": "flushed before every timed step (256 MiB write)",
+                   "M": M, "N": N, "precision": "f64", "l2": "flushed before every timed step (256 MiB write, then read back so no dirty lines remain)",
                    "parallelism": "independent instance per GPU" if ws > 1 else "single GPU"},
         "roofline": roofline,
         "path": {"algorithmic_bytes": path_bytes, "GBps": path_bytes / (ms_per_step * 1e-3) / 1e9,
@@ -308,6 +324,8 @@ def run_ours(args):
         line["e2e"] = e2e_measure(g, h, wl, dev, stream, min(K, 100), inst)
         if ws == 1:
             line["map_only"] = map_only(g, h, wl, dev, stream)
+            line["gather"] = gather_measure(g, h, dev, stream, hbm)
+            line["paper_sweep"] = paper_sweep(g, h, dev, stream)
             del wd, flush, graph
             torch.cuda.empty_cache()
             line["batched"] = batched_measure(g, h, dev, stream, hbm)
@@ -375,6 +393,64 @@ def map_only(g, h, wl, dev, stream, K=50):
             ms = statistics.median(a.elapsed_time(b) for a, b in ev)
             res[name] = {"us_per_call": ms * 1e3, "particles_per_s": N / (ms * 1e-3)}
     return res
+
+
+def gather_measure(g, h, dev, stream, hbm, reps=20):
+    """The step after resampling, x'_i = x_{r_i}: N = M = 4,194,304 particles
+    of 4 binary64 components (the bootstrap-filter size), gathered by the
+    resampled indices of the bootstrap instance."""
+    import torch
+    wl = workloads.make("bootstrap")
+    M, N, D = wl.M, wl.N, 4
+    x = torch.randn((M, D), dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    idx = torch.empty(N, dtype=torch.int32, device=dev)
+    xo = torch.empty((N, D), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        g.rs_resample_w(h.h, torch.from_numpy(wl.w).to(dev), M, N, wl.seed, 0, idx, stream=stream)
+    ms = _time_calls(lambda: g.rs_gather(h.h, x, M, D * 8, idx, N, xo, stream=stream), stream, reps)
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the gather")
+    bytes_ = 2 * N * D * 8 + 4 * N
+    return {"workload": "N=M=4,194,304 rows of 4 binary64, bootstrap indices", "us_per_call": ms * 1e3,
+            "GBps": bytes_ / (ms * 1e-3) / 1e9, "frac_of_hbm": bytes_ / (ms * 1e-3) / 1e9 / hbm,
+            "bytes_per_call": bytes_}
+
+
+def paper_sweep(g, h, dev, stream, reps=20):
+    """Figure 2's experiment shape: the sampling steps (sorted uniforms plus
+    the map, W given) for N from 1e2 to 1e4 and M/N in {1, 100, 1000}, on the
+    GPU (rs_resample_W per map) and with the oracle's serial Algorithms 3, 4
+    and 5 on the host (sorted uniforms included), weights exp(l), l~N(0,2^2)."""
+    import torch
+    import oracle
+    oracle.lib()
+    rows = []
+    for ratio in (1, 100, 1000):
+        for N in (100, 316, 1000, 3162, 10000):
+            M = N * ratio
+            w = workloads.weights_lognormal(M, 2.0, seed=1000 + N + ratio)
+            W, _ = oracle.cumulative(w)
+            Wd = torch.from_numpy(W).to(dev)
+            out = torch.empty(N, dtype=torch.int32, device=dev)
+            row = {"N": N, "M": M}
+            for name, algo in [("dac", g.RS_MAP_DAC), ("binary", g.RS_MAP_BINARY), ("linear", g.RS_MAP_LINEAR)]:
+                o = g.opts(algo=algo)
+                row["gpu_us_" + name] = 1e3 * _time_calls(
+                    lambda: g.rs_resample_W(h.h, Wd, M, N, 7, 0, out, o, stream=stream), stream, reps)
+            for name, fn in [("dac", oracle.alg5_dac_map), ("binary", oracle.alg3_binary_map),
+                             ("ccf", oracle.alg4_ccf_map)]:
+                ts = []
+                for _ in range(3):
+                    t = time.perf_counter()
+                    U = oracle.sorted_uniform(N, 7, 0)
+                    fn(W, U)
+                    ts.append(time.perf_counter() - t)
+                row["cpu_us_" + name] = 1e6 * statistics.median(ts)
+            rows.append(row)
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the sweep")
+    return {"what": "sampling steps (sorted uniforms + map, W given); GPU maps vs the oracle's serial "
+                    "Algorithms 3/4/5 on 1 host core", "rows": rows}
 
 
 def _time_calls(fn, stream, reps, warm=2):

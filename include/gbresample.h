@@ -201,6 +201,19 @@ rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int6
 rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t first, int64_t n, uint64_t* out,
                     void* stream);
 
+/* The resampled particle set (Sec. I: the filter continues with the particles
+ * the indices select): x_out[i] = x[idx[i]], i = 0..N-1, rows of row_bytes
+ * bytes.
+ *  x       [M rows] particles, row-major, device; 4-byte aligned (16-byte
+ *          aligned rows and pointers move 16 bytes per access).
+ *  idx     [N] int32 row indices (e.g. the out_idx of a resampling call).
+ *  x_out   [N rows], written; must not overlap x.
+ *  row_bytes  a positive multiple of 4 (D elements of 4 or 8 bytes).
+ * An index outside [0, M) writes a zero row and latches RS_EINVAL in the
+ * device status word (rs_get_status).  Bit-exact copy; HBM-bound. */
+rs_status rs_gather(rs_handle* h, const void* x, int64_t M, int64_t row_bytes, const int32_t* idx, int64_t N,
+                    void* x_out, void* stream);
+
 /* K independent instances (the many-filter setting of Sec. I: M_k = N_k * P_k
  * weights per filter).  Instance k owns w[w_off[k] .. w_off[k+1]) and
  * out_idx[r_off[k] .. r_off[k+1]) and draws from the Philox stream

@@ -61,6 +61,7 @@ def lib():
             "rs_cumulative": (_ST, [_P, _P, _I64, _P, _OPTS, _P]),
             "rs_map": (_ST, [_P, _P, _I64, _P, _I64, _P, _OPTS, _P]),
             "rs_philox": (_ST, [_P, _U64, _U64, _U64, _I64, _P, _P]),
+            "rs_gather": (_ST, [_P, _P, _I64, _I64, _P, _I64, _P, _P]),
             "rs_resample_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _P]),
             "rs_autotune_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _OPTS, _P]),
             "rs_trace_enable": (_ST, [_P, ctypes.c_int]),
@@ -134,6 +135,10 @@ def rs_resample_w(h, w, M, N, seed, instance, out_idx, W_out=None, o=None, strea
 
 def rs_resample_W(h, W, M, N, seed, instance, out_idx, o=None, stream=None):
     _check(h, lib().rs_resample_W(h, _ptr(W), M, N, seed, instance, _ptr(out_idx), _opt(o), _stream(stream)))
+
+
+def rs_gather(h, x, M, row_bytes, idx, N, x_out, stream=None):
+    _check(h, lib().rs_gather(h, _ptr(x), M, row_bytes, _ptr(idx), N, _ptr(x_out), _stream(stream)))
 
 
 def rs_sorted_uniform(h, N, seed, instance, U_out, o=None, stream=None):

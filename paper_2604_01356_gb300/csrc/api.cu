@@ -657,6 +657,22 @@ rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int6
   return enqueue_map(h, o, W, M, U, N, out_idx, static_cast<cudaStream_t>(stream));
 }
 
+rs_status rs_gather(rs_handle* h, const void* x, int64_t M, int64_t row_bytes, const int32_t* idx, int64_t N,
+                    void* x_out, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  if (M < 1 || M > kMaxLen) return fail(h, RS_EINVAL, "M must satisfy 1 <= M < 2^31");
+  if (N < 0 || N > kMaxLen) return fail(h, RS_EINVAL, "N must satisfy 0 <= N < 2^31");
+  if (row_bytes <= 0 || (row_bytes & 3)) return fail(h, RS_EINVAL, "row_bytes must be a positive multiple of 4");
+  if (N == 0) return RS_OK;
+  if (!x || !idx || !x_out || !aligned(x, 4) || !aligned(idx, 4) || !aligned(x_out, 4))
+    return fail(h, RS_EINVAL, "x, idx and x_out must be non-NULL 4-byte aligned device pointers");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_TRACE(h, "gather", st);
+  RS_CK(h, launch_gather(x, M, row_bytes, idx, N, x_out, h->status, st));
+  return RS_OK;
+}
+
 rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
                               const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
                               const rs_opts* opts, void* stream) {

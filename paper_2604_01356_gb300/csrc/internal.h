@@ -128,6 +128,10 @@ struct FusedLaunch {
 // device cannot hold the whole grid at once.
 cudaError_t launch_fused(bool f32, bool vec, const FusedLaunch& L, cudaStream_t st);
 
+// --- the resampled particle set x'_i = x_{r_i} ----------------------------
+cudaError_t launch_gather(const void* x, long long M, long long row_bytes, const int* idx, long long N, void* y,
+                          int* status, cudaStream_t st);
+
 // --- maps (Eq. 2; Algorithms 3, 4, 5) -------------------------------------
 cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const SegRec* seg, const SegPre* pre,
                            const SegIndex& idx, const PathConsts* consts, const void* Z, long long N, int G, int* out,
