@@ -33,7 +33,7 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
                                               uint64_t k1, uint64_t out[4]) {
   const uint64_t mA = 0xD2E7470EE14C6C93ULL, mB = 0xCA5A826395121157ULL;
   const uint64_t wA = 0x9E3779B97F4A7C15ULL, wB = 0xBB67AE8584CAA73BULL;
-#pragma unroll
+#pragma unroll 1
   for (int r = 0; r < 10; ++r) {
     if (r) {
       k0 += wA;

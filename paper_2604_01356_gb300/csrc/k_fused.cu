@@ -434,14 +434,19 @@ __device__ __forceinline__ void map_own(const T* __restrict__ w, long long M, co
   c.sh = c.len = 0;
   c.head = false;
   c.F = 0;
+  u128 z_cur = z_first;
 #pragma unroll 1
   for (long long r0 = i0; r0 < i1; r0 += 32) {
     const long long i = r0 + lane;
     const bool valid = i < i1;
     const bool w0 = threadIdx.x == 0 && r0 == i0;
     GBR_STAMP_IF(w0, 10);
+    // the next round's spacing prefixes travel while this round is mapped
+    u128 z_next = {0ULL, 0ULL};
+    if (i + 32 < i1) z_next = u128{__ldcg(&Z[i + 32].lo), __ldcg(&Z[i + 32].hi)};
     u128 key = {0ULL, 0ULL};
-    if (valid) key = map_key(cx.c, u128_add(zoff, r0 == i0 ? z_first : u128{__ldcg(&Z[i].lo), __ldcg(&Z[i].hi)}));
+    if (valid) key = map_key(cx.c, u128_add(zoff, z_cur));
+    z_cur = z_next;
     GBR_STAMP_IF(w0, 11);
     const bool in_cur = valid && c.cur >= 0 && u128_lt(c.Ps, key) && !u128_lt(c.Pn, key);
     long long s_me = c.cur;
