@@ -717,7 +717,7 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
   for (int32_t k = 0; k < K; ++k) {
     const long long Mk = wo[k + 1] - wo[k], Nk = ro[k + 1] - ro[k];
     if (Nk == 0) continue;
-    if (f32 && (Mk + kSegLen - 1) / kSegLen <= kBMaxSeg) continue;
+    if (f32 && (Mk + kSegLen - 1) / kSegLen <= kBMaxSeg && Nk <= kBMaxN) continue;
     const void* wk = static_cast<const char*>(w) + (size_t)wo[k] * esz;
     if ((s = rs_resample_w(h, wk, Mk, Nk, seed, (uint64_t)k, out_idx + ro[k], nullptr, &one, stream))) return s;
   }

@@ -138,6 +138,7 @@ cudaError_t launch_map_seg(bool f32, bool vec, const void* w, long long M, const
                            cudaStream_t st);
 // --- batched persistent path (K instances, one CTA per instance) ----------
 constexpr int kBMaxSeg = 512;     // segments of the largest instance a CTA takes (M_k <= 262,144)
+constexpr int kBMaxN = 2048;      // samples of the largest instance a CTA takes
 constexpr int kSortMax = 16384;   // batches up to this size are ordered by M_k on the device
 cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cudaStream_t st);
 cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,

@@ -9,21 +9,46 @@
 //                     (Eq. 3 at the segment level), kept in shared memory;
 //   B  prefixes       the instance's segment sums on its global grid, scanned
 //                     exactly as 128-bit integers (shared memory);
-//   C  total Z_{N+1}  all N+1 spacings of Algorithm 1 summed exactly;
-//   D  map            the spacings again, in chunks of 4 per thread, scanned
-//                     into Z_i; key_i = ceil(Z_i S / Z_{N+1}); the segment by
-//                     binary search over the shared-memory prefixes; the
-//                     element inside the segment from the segment's exact
-//                     prefixes - by a warp-wide count when few samples fall
-//                     in the segment, else by per-lane binary search over the
-//                     prefixes staged in shared memory (the leaf threshold).
+//   C  spacings       all N+1 spacings of Algorithm 1 (or of the strata
+//                     points) once, scanned exactly into Z_i (shared memory)
+//                     and Z_{N+1}; then key_i = ceil(Z_i S / Z_{N+1});
+//   D  map            segment-major: warp w takes a contiguous range of
+//                     segments and the samples whose keys fall in them (the
+//                     keys are sorted); each segment with samples is loaded
+//                     once, the next one travelling meanwhile, and its samples
+//                     are resolved from its exact prefixes - by a warp-wide
+//                     count when few samples fall in it, else by per-lane
+//                     binary search over the prefixes staged in shared memory
+//                     (the leaf threshold).
 // Every step uses the single-instance path's arithmetic (same segment sums,
 // grid, spacings, keys and in-segment decisions), so the indices equal those
 // of rs_resample_w on each instance bit for bit.
 //
-// Instances with more than kBMaxSeg segments are not processed here (the host
-// sends them through the multi-CTA single-instance path).
+// Instances with more than kBMaxSeg segments or kBMaxN samples are not
+// processed here (the host sends them through the single-instance path).
 #include "seg_common.cuh"
+
+// Phase timestamps (profiling builds only, -DGBR_PHASE_STAMPS): %globaltimer
+// at the phase ends of the first instance each CTA takes, 8 slots per CTA,
+// in a buffer set by rs_dbg_set_batch_stamps.
+#ifdef GBR_PHASE_STAMPS
+namespace gbr {
+__device__ unsigned long long* g_bstamps = nullptr;
+}
+extern "C" int rs_dbg_set_batch_stamps(void* p) { return (int)cudaMemcpyToSymbol(gbr::g_bstamps, &p, sizeof(p)); }
+#define GBR_BSTAMP(first, k)                                               \
+  do {                                                                     \
+    if ((first) && threadIdx.x == 0 && gbr::g_bstamps) {                   \
+      unsigned long long t_;                                               \
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_));               \
+      gbr::g_bstamps[blockIdx.x * 8 + (k)] = t_;                           \
+    }                                                                      \
+  } while (0)
+#else
+#define GBR_BSTAMP(first, k) \
+  do {                       \
+  } while (0)
+#endif
 
 namespace gbr {
 
@@ -35,6 +60,7 @@ struct BatchSmem {
   unsigned long long F[kBMaxSeg];  // segment sums on their own grids
   int E[kBMaxSeg];                 // segment exponents
   unsigned long long pref[kWarps][kSeg];  // staged in-segment prefixes (leaf search)
+  u128 key[kBMaxN];                 // Z_i, then the keys ceil(Z_i S / Z_{N+1})
   u128 wsum[kWarps];
   xf c;
   int emax_w[kWarps];
@@ -82,6 +108,8 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
   BatchSmem<kWarps>& sm = *reinterpret_cast<BatchSmem<kWarps>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+  bool first = true;
+  GBR_BSTAMP(true, 0);
   while (true) {
     __syncthreads();  // the previous instance is done with shared memory
     if (tid == 0) sm.item = (int)atomicAdd(queue, 1u);
@@ -95,11 +123,12 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
     const long long Nk = r_off[k + 1] - rb;
     if (Nk <= 0 || Mk <= 0) continue;
     const long long nseg = (Mk + kSeg - 1) / kSeg;
-    if (nseg > kBMaxSeg) continue;  // left to the single-instance path
+    if (nseg > kBMaxSeg || Nk > kBMaxN) continue;  // left to the single-instance path
     const float* wk = w + wb;
     const bool vec = (reinterpret_cast<uintptr_t>(wk) & 15) == 0;
     int* outk = out + rb;
 
+    GBR_BSTAMP(first, 1);
     // ---- A: exact segment sums, two segments in flight per warp --------------
     int em = 0;
     for (int s0 = warp; s0 < nseg; s0 += 2 * kWarps) {
@@ -135,6 +164,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
 #pragma unroll
     for (int i = 0; i < kWarps; ++i) Emax = max(Emax, sm.emax_w[i]);
 
+    GBR_BSTAMP(first, 2);
     // ---- B: grid prefixes (consecutive segments per thread) -----------------
     constexpr int kPer = (kBMaxSeg + kThreads - 1) / kThreads;
     u128 v[kPer];
@@ -160,152 +190,152 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
       continue;
     }
 
-    // ---- C: Z_{N+1}, the sum of all N+1 spacings ----------------------------
+    GBR_BSTAMP(first, 3);
+    // ---- C: all N+1 spacings once, their exact prefixes Z_i kept -------------
     const long long ndraw = Nk + 1;
-    u128 zsum = {0ULL, 0ULL};
-    if (scheme == kSchemeMultinomial)
-      for (long long d0 = (long long)tid * 4; d0 < ndraw; d0 += kChunk) {
-        uint64_t wd[4];
-        philox4x64_10((uint64_t)(d0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (d0 + q < ndraw) zsum = u128_add(zsum, spacing_fixed<true>(wd[q], nullptr));
-      }
-    else if (tid == 0)
-      zsum = u128{0ULL, (unsigned long long)Nk << 24};  // the strata spacings telescope to N
-    u128 Ztot;
-    (void)block_excl_scan<kWarps>(zsum, sm.wsum, Ztot);
-    u128 vsys = {0ULL, 0ULL};  // systematic: the one draw v_0
-    if (scheme == kSchemeSystematic) {
-      uint64_t w0[4];
-      philox4x64_10(0ULL, 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, w0);
-      vsys = draw_fixed<true>(w0[0]);
-    }
-    if (tid == 0) compute_c(&sm.c, S, Ztot);
-    __syncthreads();
-    const xf c = sm.c;
-
-    // ---- D: Z_i, keys and the map, 4 rounds of 32 samples per warp ----------
     u128 carry = {0ULL, 0ULL};
-    for (long long cb = 0; cb < Nk; cb += kChunk) {
-      const long long wbase = cb + (long long)warp * 128;  // this warp's 128 draws
+#pragma unroll 1
+    for (long long d0 = 0; d0 < ndraw; d0 += kChunk) {
+      const long long k0 = d0 + 4LL * tid;  // one Philox block per thread
       uint64_t wd[4];
-      philox4x64_10((uint64_t)((wbase + 4 * lane) / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
-      u128 f[4], inc[4];
-      u128 wtot = {0ULL, 0ULL};
+      philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
+      u128 f[4];
+      block_spacings<true>(scheme, k0, ndraw, seed, (unsigned long long)k, wd, nullptr, f);
+      u128 run = {0ULL, 0ULL}, inc[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int src = 8 * r + (lane >> 2);
-        const uint64_t x0 = __shfl_sync(0xFFFFFFFFu, wd[0], src);
-        const uint64_t x1 = __shfl_sync(0xFFFFFFFFu, wd[1], src);
-        const uint64_t x2 = __shfl_sync(0xFFFFFFFFu, wd[2], src);
-        const uint64_t x3 = __shfl_sync(0xFFFFFFFFu, wd[3], src);
-        const int wq = lane & 3;
-        const uint64_t word = wq == 0 ? x0 : wq == 1 ? x1 : wq == 2 ? x2 : x3;
-        const long long d = wbase + 32 * r + lane;
-        if (scheme == kSchemeMultinomial) {
-          f[r] = d < Nk ? spacing_fixed<true>(word, nullptr) : u128{0ULL, 0ULL};
-        } else {
-          // word d - 1: the previous word of this block, the last word of the
-          // previous lane's block, or (draw 32 r of the chunk) recomputed
-          uint64_t wp = __shfl_sync(0xFFFFFFFFu, wd[3], src > 0 ? src - 1 : 0);
-          if (wq == 1) wp = x0;
-          if (wq == 2) wp = x1;
-          if (wq == 3) wp = x2;
-          if (wq == 0 && src == 0 && d > 0) {
-            uint64_t pw[4];
-            philox4x64_10((uint64_t)(d / 4 - 1), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, pw);
-            wp = pw[3];
-          }
-          const u128 vk = scheme == kSchemeSystematic ? vsys : draw_fixed<true>(word);
-          const u128 vp = scheme == kSchemeSystematic ? vsys : draw_fixed<true>(wp);
-          f[r] = d < Nk ? strata_spacing(d, Nk, vk, vp) : u128{0ULL, 0ULL};
-        }
-        inc[r] = warp_incl_scan_v(f[r], lane);
-        const u128 t = shfl_v(inc[r], 31);
-        inc[r] = u128_add(inc[r], wtot);  // plus the earlier rounds of this warp
-        wtot = u128_add(wtot, t);
+      for (int q = 0; q < 4; ++q) {
+        run = u128_add(run, f[q]);
+        inc[q] = run;
       }
       u128 ctot;
-      const u128 woff = block_excl_scan<kWarps>(lane == 0 ? wtot : u128{0ULL, 0ULL}, sm.wsum, ctot);
-      const u128 base = u128_add(carry, shfl_v(woff, 0));
+      const u128 off = u128_add(carry, block_excl_scan<kWarps>(run, sm.wsum, ctot));
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (k0 + q < Nk) sm.key[k0 + q] = u128_add(off, inc[q]);
       carry = u128_add(carry, ctot);
+    }
+    if (tid == 0) compute_c(&sm.c, S, carry);  // carry = Z_{N+1}
+    __syncthreads();
+    const xf c = sm.c;
+    GBR_BSTAMP(first, 4);
+    for (long long i = tid; i < Nk; i += kThreads) sm.key[i] = map_key(c, sm.key[i]);
+    __syncthreads();
+
+    // ---- D: the map, segment-major -------------------------------------------
+    // Warp w takes segments [a, b); a sample belongs to segment s when
+    // P_s < key <= P_{s+1} (the last segment also takes keys above S).  Each
+    // segment with samples is loaded once (the next one travels meanwhile),
+    // its exact prefixes are staged in shared memory and every sample of it
+    // is resolved by a binary search over them.
+    {
+      const int sa = (int)(nseg * warp / kWarps), sb = (int)(nseg * (warp + 1) / kWarps);
+      // first sample of segment sa: keys are sorted
+      long long i = 0;
+      {
+        long long lo = 0, hi = Nk;
+        const u128 Pa = sm.pre[sa];
+        while (lo < hi) {
+          const long long mid = (lo + hi) >> 1;
+          if (!u128_lt(Pa, sm.key[mid])) lo = mid + 1;
+          else hi = mid;
+        }
+        i = lo;
+      }
+      unsigned long long* sp = sm.pref[warp];
+      Bits bn[kSegV];
+      int pf = -1;
 #pragma unroll 1
-      for (int r = 0; r < 4; ++r) {
-        const long long i = wbase + 32 * r + lane;  // sample index (Z_{i+1})
-        const bool valid = i < Nk;
-        if (!__any_sync(0xFFFFFFFFu, valid)) break;
-        const u128 key = map_key(c, u128_add(base, inc[r]));
-        // last segment with P_s < key (P_0 = 0 < key)
-        int s_me = 0;
-        if (valid) {
-          int lo = 0, hi = (int)nseg;
+      for (int sc = sa; sc < sb && i < Nk; ++sc) {
+        const bool last = sc == (int)nseg - 1;
+        const u128 Pn = sm.pre[sc + 1];
+        long long ie = i;  // samples [i, ie) fall in segment sc
+        if (last) {
+          ie = Nk;
+        } else {
+          long long lo = i, hi = Nk;
           while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (u128_lt(sm.pre[mid], key)) lo = mid + 1;
+            const long long mid = (lo + hi) >> 1;
+            if (!u128_lt(Pn, sm.key[mid])) lo = mid + 1;
             else hi = mid;
           }
-          s_me = lo > 0 ? lo - 1 : 0;
+          ie = lo;
         }
-        unsigned pend = __ballot_sync(0xFFFFFFFFu, valid);
-        while (pend) {
-          const int sc = __shfl_sync(0xFFFFFFFFu, s_me, __ffs(pend) - 1);
-          const unsigned grp = __ballot_sync(0xFFFFFFFFu, valid && s_me == sc) & pend;
-          const bool mine = (grp >> lane) & 1u;
-          Bits b[kSegV];
-          if (vec) load_seg_blocked<float, true>(wk, (long long)sc * kSeg, Mk, lane, b);
-          else load_seg_blocked<float, false>(wk, (long long)sc * kSeg, Mk, lane, b);
-          const uint32_t E = (uint32_t)sm.E[sc];
-          uint64_t pref[kSegV];
-          seg_prefixes<float>(b, E, lane, pref);
-          unsigned long long Kq = 0;
-          if (mine) {
-            const u128 Ps = sm.pre[sc];
+        if (ie == i) continue;
+        Bits b[kSegV];
+        if (pf == sc) {
+#pragma unroll
+          for (int q = 0; q < kSegV; ++q) b[q] = bn[q];
+        } else if (vec) {
+          load_seg_blocked<float, true>(wk, (long long)sc * kSeg, Mk, lane, b);
+        } else {
+          load_seg_blocked<float, false>(wk, (long long)sc * kSeg, Mk, lane, b);
+        }
+        pf = -1;
+        if (sc + 1 < sb) {  // the next segment's weights travel while this one is resolved
+          if (vec) load_seg_blocked<float, true>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+          else load_seg_blocked<float, false>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+          pf = sc + 1;
+        }
+        const uint32_t E = (uint32_t)sm.E[sc];
+        const unsigned long long Fs = sm.F[sc];
+        const u128 Ps = sm.pre[sc];
+        const int sh = (int)E - Emax + kGridHead;
+        const long long rem_len = Mk - (long long)sc * kSeg;
+        const int len = (int)(rem_len < kSeg ? rem_len : kSeg);
+        uint64_t pref[kSegV];
+        seg_prefixes<float>(b, E, lane, pref);
+        if (ie - i <= leaf_T) {
+          // a few samples: a warp-wide count over the prefixes in registers
+          // (the linear-walk leaf)
+#pragma unroll 1
+          for (long long j = i; j < ie; ++j) {
+            const u128 key = sm.key[j];
             const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
-            Kq = ceil_units(rem, (int)E - Emax + kGridHead, sm.F[sc]);
-          }
-          int cnt = 0;
-          if (__popc(grp) <= leaf_T) {
-            unsigned g = grp;
-            while (g) {
-              const int j = __ffs(g) - 1;
-              g &= g - 1;
-              const unsigned long long Kj = __shfl_sync(0xFFFFFFFFu, Kq, j);
-              int cj = 0;
+            const unsigned long long Kq = ceil_units(rem, sh, Fs);
+            int cnt = 0;
 #pragma unroll
-              for (int q = 0; q < kSegV; ++q) cj += pref[q] < Kj ? 1 : 0;
+            for (int q = 0; q < kSegV; ++q) cnt += pref[q] < Kq ? 1 : 0;
 #pragma unroll
-              for (int o = 16; o; o >>= 1) cj += __shfl_xor_sync(0xFFFFFFFFu, cj, o);
-              if (lane == j) cnt = cj;
+            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            if (lane == 0) {
+              const int jj = cnt < len ? cnt : len - 1;
+              long long idx = (long long)sc * kSeg + jj;
+              if (idx > Mk - 1) idx = Mk - 1;
+              outk[j] = (int)idx;
             }
-          } else {
-            unsigned long long* sp = sm.pref[warp];
+          }
+        } else {
+          // the binary-search leaf over prefixes staged in shared memory
+          __syncwarp();
 #pragma unroll
-            for (int q = 0; q < kSegV; ++q) sp[lane * kSegV + q] = pref[q];
-            __syncwarp();
-            if (mine) {  // number of prefixes below K (they are non-decreasing)
-              int lo = 0, hi = kSeg;
+          for (int q = 0; q < kSegV; ++q) sp[lane * kSegV + q] = pref[q];
+          __syncwarp();
+#pragma unroll 1
+          for (long long j0 = i; j0 < ie; j0 += 32) {
+            const long long j = j0 + lane;
+            if (j < ie) {
+              const u128 key = sm.key[j];
+              const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
+              const unsigned long long Kq = ceil_units(rem, sh, Fs);
+              int lo = 0, hi = kSeg;  // prefixes below K (non-decreasing)
               while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
                 if (sp[mid] < Kq) lo = mid + 1;
                 else hi = mid;
               }
-              cnt = lo;
+              const int jj = lo < len ? lo : len - 1;
+              long long idx = (long long)sc * kSeg + jj;
+              if (idx > Mk - 1) idx = Mk - 1;
+              outk[j] = (int)idx;
             }
-            __syncwarp();
           }
-          if (mine) {
-            const long long rem_len = Mk - (long long)sc * kSeg;
-            const int len = (int)(rem_len < kSeg ? rem_len : kSeg);
-            const int j = cnt < len ? cnt : len - 1;
-            long long idx = (long long)sc * kSeg + j;
-            if (idx > Mk - 1) idx = Mk - 1;
-            outk[i] = (int)idx;
-          }
-          pend &= ~grp;
+          __syncwarp();
         }
+        i = ie;
       }
     }
+    GBR_BSTAMP(first, 5);
+    first = false;
   }
 }
 
