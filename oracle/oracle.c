@@ -293,6 +293,22 @@ int64_t orc_alg5_dac_map(const double* W, int64_t M, const double* U, int64_t N,
  * w_is_f32 selects binary32 weights; single selects binary32 draws (the
  * compensated-binary32 path's stream), both evaluated here in binary64.
  * W_out, U_out may be NULL.  Returns the orc_cumulative status. */
+/* Weights from log-weights, the step the paper places before resampling
+ * (Sec. I: the filter carries log-likelihood weights): w_j = exp(l_j - m),
+ * m = max_k l_k, so the largest weight is 1 and nothing overflows; -inf
+ * gives a zero weight.  Returns 1 for a NaN or +inf log-weight, 2 when every
+ * l_j is -inf (zero total), else 0. */
+int orc_softmax_weights(const double* l, int64_t M, double* w) {
+  double m = -INFINITY;
+  for (int64_t j = 0; j < M; ++j) {
+    if (isnan(l[j]) || l[j] == INFINITY) return 1;
+    if (l[j] > m) m = l[j];
+  }
+  if (m == -INFINITY) return 2;
+  for (int64_t j = 0; j < M; ++j) w[j] = exp(l[j] - m);
+  return 0;
+}
+
 /* Stratified and systematic uniforms, the variants the paper's concluding
  * section says the method extends to: N points, one per stratum
  * ((i-1)/N, i/N], i = 1..N, with the same draws v_k as Algorithm 1:

@@ -56,6 +56,8 @@ def lib():
         L.orc_alg5_dac_map.restype = _i64
         L.orc_resample.argtypes = [_p, _int, _i64, _i64, _u64, _u64, _int, _p, _p, _p]
         L.orc_resample.restype = _int
+        L.orc_softmax_weights.argtypes = [_p, _i64, _p]
+        L.orc_softmax_weights.restype = _int
         L.orc_scheme_uniform.argtypes = [_u64, _u64, _i64, _int, _int, _p]
         L.orc_scheme_uniform.restype = None
         L.orc_resample_scheme.argtypes = [_p, _int, _i64, _i64, _u64, _u64, _int, _int, _p, _p, _p]
@@ -105,6 +107,16 @@ def sorted_uniform(N, seed, instance=0, single=False):
     U = np.zeros(max(N, 1), dtype=np.float64)
     lib().orc_sorted_uniform(seed, instance, N, int(bool(single)), _ptr(U))
     return U[:N]
+
+
+def softmax_weights(l):
+    """w_j = exp(l_j - max l) in binary64 (the largest weight is 1)."""
+    ll = _f64(l)
+    w = np.zeros(max(ll.shape[0], 1), dtype=np.float64)
+    rc = lib().orc_softmax_weights(_ptr(ll), ll.shape[0], _ptr(w))
+    if rc:
+        raise OracleError(rc)
+    return w[: ll.shape[0]]
 
 
 SCHEMES = {"multinomial": 0, "stratified": 1, "systematic": 2}

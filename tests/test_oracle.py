@@ -368,3 +368,36 @@ def test_stratified_counts_within_one_and_unbiased():
 def test_scheme_zero_is_algorithm_1():
     U0 = oracle.scheme_uniform(333, 9, 2, "multinomial")
     assert np.array_equal(U0, oracle.sorted_uniform(333, 9, 2))
+
+
+# ------------------------------------------------------ log-weight input ----
+def test_softmax_shift_invariance_and_max():
+    rng = np.random.default_rng(3)
+    l = rng.normal(0.0, 10.0, size=5000)
+    w = oracle.softmax_weights(l)
+    assert w.max() == 1.0 and np.all(w >= 0)
+    # adding a constant to every log-weight leaves the cumulative weights unchanged
+    W1, _ = oracle.cumulative(w)
+    W2, _ = oracle.cumulative(oracle.softmax_weights(l + 1234.5))
+    assert np.max(np.abs(W1 - W2)) <= 1e-13
+
+
+def test_softmax_closed_forms():
+    # equal log-weights: W_j = j / M exactly (M a power of two)
+    W, _ = oracle.cumulative(oracle.softmax_weights(np.full(1024, -7.25)))
+    assert np.array_equal(W, np.arange(1, 1025) / 1024.0)
+    # l = (0, log 3): w proportional to (1, 3) -> W = (1/4, 1)
+    W, _ = oracle.cumulative(oracle.softmax_weights(np.array([0.0, np.log(3.0)])))
+    assert abs(W[0] - 0.25) <= 1e-16 and W[1] == 1.0
+    # -inf gives a zero weight, never drawn
+    w = oracle.softmax_weights(np.array([-np.inf, 0.0, -np.inf]))
+    assert np.array_equal(w, [0.0, 1.0, 0.0])
+
+
+def test_softmax_invalid():
+    with pytest.raises(oracle.OracleError):
+        oracle.softmax_weights(np.array([0.0, np.nan]))
+    with pytest.raises(oracle.OracleError):
+        oracle.softmax_weights(np.array([0.0, np.inf]))
+    with pytest.raises(oracle.OracleError):
+        oracle.softmax_weights(np.array([-np.inf, -np.inf]))
