@@ -201,6 +201,23 @@ rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int6
 rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t first, int64_t n, uint64_t* out,
                     void* stream);
 
+/* Weights from log-weights (the filter of Sec. I carries log-likelihoods):
+ * w_out[j] = exp(logw[j] - max_k logw[k]), binary64, the largest weight 1.
+ *  logw  [M] binary64 log-weights, device; -inf gives a zero weight.
+ *  w_out [M] binary64, written (may not overlap logw).
+ * Computed without binary64 arithmetic per element: the exponent is
+ * evaluated in binary32 pairs (relative error about 2^-44 of the binary64
+ * value; subnormal results are truncated).  NaN, +inf or |l| >= 2^126
+ * latch RS_ENONFINITE; all -inf latches RS_EZEROSUM (rs_get_status).
+ * Two passes over logw (maximum, then exponent) and one write of w_out. */
+rs_status rs_softmax_weights(rs_handle* h, const double* logw, int64_t M, double* w_out, void* stream);
+
+/* rs_resample_w from log-weights: rs_softmax_weights into the handle's
+ * workspace (M * 8 bytes more), then the whole path (Eq. 3 + Alg. 1 + Eq. 2).
+ * opts as for rs_resample_w; opts->prec must be RS_F64. */
+rs_status rs_resample_logw(rs_handle* h, const double* logw, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                           int32_t* out_idx, const rs_opts* opts, void* stream);
+
 /* The resampled particle set (Sec. I: the filter continues with the particles
  * the indices select): x_out[i] = x[idx[i]], i = 0..N-1, rows of row_bytes
  * bytes.

@@ -13,5 +13,6 @@ from ._binding import (  # noqa: F401
     ResampleError, Handle, lib, library_path, opts,
     rs_create, rs_destroy, rs_get_status, rs_last_error, rs_version,
     rs_resample_w, rs_resample_W, rs_sorted_uniform, rs_sorted_uniform_static, rs_cumulative, rs_map, rs_philox, rs_gather,
+    rs_softmax_weights, rs_resample_logw,
     rs_resample_batched, rs_autotune_batched, rs_trace_enable, rs_trace_collect, rs_trace_report, rs_trace_reset,
 )

@@ -62,6 +62,8 @@ def lib():
             "rs_map": (_ST, [_P, _P, _I64, _P, _I64, _P, _OPTS, _P]),
             "rs_philox": (_ST, [_P, _U64, _U64, _U64, _I64, _P, _P]),
             "rs_gather": (_ST, [_P, _P, _I64, _I64, _P, _I64, _P, _P]),
+            "rs_softmax_weights": (_ST, [_P, _P, _I64, _P, _P]),
+            "rs_resample_logw": (_ST, [_P, _P, _I64, _I64, _U64, _U64, _P, _OPTS, _P]),
             "rs_resample_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _P]),
             "rs_autotune_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _OPTS, _P]),
             "rs_trace_enable": (_ST, [_P, ctypes.c_int]),
@@ -135,6 +137,14 @@ def rs_resample_w(h, w, M, N, seed, instance, out_idx, W_out=None, o=None, strea
 
 def rs_resample_W(h, W, M, N, seed, instance, out_idx, o=None, stream=None):
     _check(h, lib().rs_resample_W(h, _ptr(W), M, N, seed, instance, _ptr(out_idx), _opt(o), _stream(stream)))
+
+
+def rs_softmax_weights(h, logw, M, w_out, stream=None):
+    _check(h, lib().rs_softmax_weights(h, _ptr(logw), M, _ptr(w_out), _stream(stream)))
+
+
+def rs_resample_logw(h, logw, M, N, seed, instance, out_idx, o=None, stream=None):
+    _check(h, lib().rs_resample_logw(h, _ptr(logw), M, N, seed, instance, _ptr(out_idx), _opt(o), _stream(stream)))
 
 
 def rs_gather(h, x, M, row_bytes, idx, N, x_out, stream=None):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgbresample.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["api.cu", "k_uniform.cu", "k_weights.cu", "k_map.cu", "k_batched.cu", "k_fused.cu", "k_gather.cu", "static_uniform.cu"]
+SOURCES = ["api.cu", "k_uniform.cu", "k_weights.cu", "k_map.cu", "k_batched.cu", "k_fused.cu", "k_gather.cu", "k_logw.cu", "static_uniform.cu"]
 HEADERS = ["common.cuh", "internal.h", "seg_common.cuh", "map_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -657,6 +657,44 @@ rs_status rs_map(rs_handle* h, const double* W, int64_t M, const double* U, int6
   return enqueue_map(h, o, W, M, U, N, out_idx, static_cast<cudaStream_t>(stream));
 }
 
+rs_status rs_softmax_weights(rs_handle* h, const double* logw, int64_t M, double* w_out, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  if (M < 1 || M > kMaxLen) return fail(h, RS_EINVAL, "M must satisfy 1 <= M < 2^31");
+  if (!logw || !w_out || !aligned(logw, 8) || !aligned(w_out, 8))
+    return fail(h, RS_EINVAL, "logw and w_out must be non-NULL 8-byte aligned device pointers");
+  if ((s = ensure_ws(h, 256))) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RS_TRACE(h, "softmax", st);
+  RS_CK(h, launch_softmax_weights(logw, M, w_out, at<unsigned long long>(h, 0), h->status, st));
+  return RS_OK;
+}
+
+rs_status rs_resample_logw(rs_handle* h, const double* logw, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
+                           int32_t* out_idx, const rs_opts* opts, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  Opts o;
+  if ((s = read_opts(h, opts, &o, RS_F64))) return s;
+  if (o.prec != RS_F64) return fail(h, RS_EINVAL, "log-weights are binary64 (opts.prec must be RS_F64)");
+  if ((s = check_sizes(h, M, N))) return s;
+  if (!logw || !aligned(logw, 8)) return fail(h, RS_EINVAL, "logw must be a non-NULL 8-byte aligned pointer");
+  if (N > 0 && (!out_idx || !aligned(out_idx, 4))) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  if (N == 0) return RS_OK;
+  // the weights go to the end of the workspace, beyond the regions of the call
+  const Plan p = make_plan(M, N, true, true, false, false);
+  const size_t o_w = (p.bytes + 255) & ~size_t(255);
+  const size_t o_key = o_w + (((size_t)M * 8 + 255) & ~size_t(255));
+  if ((s = ensure_ws(h, o_key + 256))) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* w = at<double>(h, o_w);
+  {
+    RS_TRACE(h, "softmax", st);
+    RS_CK(h, launch_softmax_weights(logw, M, w, at<unsigned long long>(h, o_key), h->status, st));
+  }
+  return rs_resample_w(h, w, M, N, seed, instance, out_idx, nullptr, opts, stream);
+}
+
 rs_status rs_gather(rs_handle* h, const void* x, int64_t M, int64_t row_bytes, const int32_t* idx, int64_t N,
                     void* x_out, void* stream) {
   rs_status s = check_handle(h);

@@ -128,6 +128,11 @@ struct FusedLaunch {
 // device cannot hold the whole grid at once.
 cudaError_t launch_fused(bool f32, bool vec, const FusedLaunch& L, cudaStream_t st);
 
+// --- weights from log-weights: w_j = exp(l_j - max l) ---------------------
+// mkey: one 8-byte word of scratch (device).
+cudaError_t launch_softmax_weights(const double* l, long long M, double* w, unsigned long long* mkey, int* status,
+                                   cudaStream_t st);
+
 // --- the resampled particle set x'_i = x_{r_i} ----------------------------
 cudaError_t launch_gather(const void* x, long long M, long long row_bytes, const int* idx, long long N, void* y,
                           int* status, cudaStream_t st);
