@@ -325,6 +325,7 @@ def run_ours(args):
         if ws == 1:
             line["map_only"] = map_only(g, h, wl, dev, stream)
             line["gather"] = gather_measure(g, h, dev, stream, hbm)
+            line["logw"] = logw_measure(g, h, dev, stream, hbm)
             line["paper_sweep"] = paper_sweep(g, h, dev, stream)
             del wd, flush, graph
             torch.cuda.empty_cache()
@@ -414,6 +415,26 @@ def gather_measure(g, h, dev, stream, hbm, reps=20):
     return {"workload": "N=M=4,194,304 rows of 4 binary64, bootstrap indices", "us_per_call": ms * 1e3,
             "GBps": bytes_ / (ms * 1e-3) / 1e9, "frac_of_hbm": bytes_ / (ms * 1e-3) / 1e9 / hbm,
             "bytes_per_call": bytes_}
+
+
+def logw_measure(g, h, dev, stream, hbm, reps=20):
+    """The engmf instance from its log-weights (l ~ Normal(0, 2^2), binary64):
+    rs_resample_logw = the weights exp(l - max l) (maximum pass, exponent
+    pass writing w) and the cooperative path on w."""
+    import torch
+    c = workloads.CONFIGS["engmf"]
+    M, N = c["M"], c["N"]
+    l = torch.from_numpy(np.random.default_rng(c["seed"]).normal(0.0, 2.0, size=M)).to(dev)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    ms = _time_calls(lambda: g.rs_resample_logw(h.h, l, M, N, 12, 0, out, stream=stream), stream, reps)
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the log-weight run")
+    alg = 8 * M + 4 * N
+    moved = 8 * M * 4 + 4 * N  # max pass, exponent pass (read + write), the path's read
+    return {"workload": "engmf from log-weights: M=16,777,216 binary64 l~Normal(0,2^2), N=4,096",
+            "us_per_call": ms * 1e3, "particles_per_s": N / (ms * 1e-3),
+            "GBps_algorithmic": alg / (ms * 1e-3) / 1e9, "frac_of_hbm_algorithmic": alg / (ms * 1e-3) / 1e9 / hbm,
+            "GBps_moved": moved / (ms * 1e-3) / 1e9}
 
 
 def paper_sweep(g, h, dev, stream, reps=20):

@@ -586,8 +586,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     mbar_expect_tx(&s_full[st], bytes);
     bulk_g2s(s_dyn + (size_t)st * kStageBytes, w + sa * kSeg, bytes, &s_full[st], pol);  // one copy per stage
   };
-  if (kVec && tid == 0)
-    for (long long it = 0; it < n_it && it < kStages; ++it) issue(it);
+  if (kVec && tid == 0 && n_it > 0) issue(0);
   GBR_STAMP(14);
   if (tid == kFThreads - 32) {
     // fetch the code of the once-per-call scalar steps (reciprocal, product)
@@ -646,6 +645,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
       ztot = u128_add(ztot, tot);
     }
   }
+  if (kVec && tid == 0)
+    for (long long it = 1; it < n_it && it < kStages; ++it) issue(it);
   GBR_STAMP(1);
 
   // ---- phase 1b: the CTA's segments ------------------------------------------
