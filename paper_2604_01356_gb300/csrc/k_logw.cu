@@ -43,10 +43,17 @@ __global__ void __launch_bounds__(kLThreads) k_logw_max(const unsigned long long
   unsigned long long best = 0;
   bool bad = false;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const unsigned long long b = __ldg(l + j);
-    bad |= bad_logw(b);
-    best = max(best, bad_logw(b) ? 0ULL : order_key(b));
+  // four independent coalesced loads in flight per thread
+#pragma unroll 1
+  for (long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += 4 * stride) {
+    unsigned long long b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = j0 + q * stride < M ? __ldg(l + j0 + q * stride) : 0xFFF0000000000000ULL;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bad |= bad_logw(b[q]);
+      best = max(best, bad_logw(b[q]) ? 0ULL : order_key(b[q]));
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) best = max(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
@@ -164,16 +171,24 @@ __global__ void __launch_bounds__(kLThreads) k_logw_exp(const unsigned long long
   if (none && blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, ST_EZEROSUM);
   const f3 m = f64_split(mb);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < M; j += stride) {
-    const unsigned long long b = __ldg(l + j);
-    unsigned long long out = 0ULL;
-    if (!none && !bad_logw(b) && b != 0xFFF0000000000000ULL) {
-      const f3 lx = f64_split(b);
-      const df x = df_two_sum(lx.h, -m.h);  // l - m = x.hi + x.lo + (lx.m - m.m) + (lx.t - m.t), exactly
-      if (x.hi == 0.0f && lx.m == m.m && lx.t == m.t) out = 0x3FF0000000000000ULL;  // l_j = m: weight 1
-      else out = exp_neg_bits(x.hi, x.lo, lx.m, -m.m, lx.t, -m.t, T);
+  // four independent coalesced elements per thread: loads in flight together,
+  // the four exponentials interleaved
+#pragma unroll 1
+  for (long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; j0 < M; j0 += 4 * stride) {
+    unsigned long long b[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = j0 + q * stride < M ? __ldg(l + j0 + q * stride) : 0xFFF0000000000000ULL;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned long long out = 0ULL;
+      if (!none && !bad_logw(b[q]) && b[q] != 0xFFF0000000000000ULL) {
+        const f3 lx = f64_split(b[q]);
+        const df x = df_two_sum(lx.h, -m.h);  // l - m = x.hi + x.lo + (lx.m - m.m) + (lx.t - m.t), exactly
+        if (x.hi == 0.0f && lx.m == m.m && lx.t == m.t) out = 0x3FF0000000000000ULL;  // l_j = m: weight 1
+        else out = exp_neg_bits(x.hi, x.lo, lx.m, -m.m, lx.t, -m.t, T);
+      }
+      if (j0 + q * stride < M) w[j0 + q * stride] = out;
     }
-    w[j] = out;
   }
 }
 
@@ -184,7 +199,7 @@ cudaError_t launch_softmax_weights(const double* l, long long M, double* w, unsi
   if (M <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(mkey, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  long long blocks = (M + kLThreads - 1) / kLThreads;
+  long long blocks = (M + 4LL * kLThreads - 1) / (4LL * kLThreads);
   const long long cap = (long long)num_sms() * 8;
   if (blocks > cap) blocks = cap;
   k_logw_max<<<(unsigned)blocks, kLThreads, 0, st>>>(reinterpret_cast<const unsigned long long*>(l), M, mkey, status);
