@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-measurements (e2e, map only, batched, bootstrap, stress)")
+    ap.add_argument("--path", choices=["fused", "multikernel"], default="fused",
+                    help="rs_resample_w as one cooperative launch (default) or through the "
+                         "multi-kernel path (identical indices; for profiling and comparison)")
     return ap.parse_args()
 
 
@@ -241,8 +244,10 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     inst = rank_instance(rank)
 
+    o_path = g.opts(debug_flags=2) if args.path == "multikernel" else None
+
     def step(s):
-        g.rs_resample_w(h.h, wd, M, N, seed, inst, out, None, None, stream=s)
+        g.rs_resample_w(h.h, wd, M, N, seed, inst, out, None, o_path, stream=s)
 
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
@@ -311,7 +316,8 @@ def run_ours(args):
         "config": {"workload": "engmf: M=16,777,216 binary64 weights exp(l - max l), l~Normal(0,2^2); N=4,096; "
                                "rs_resample_w (Eq.3 + Alg.1 + segmented DaC map) as a CUDA graph",
                    "M": M, "N": N, "precision": "f64", "l2": "flushed before every timed step (256 MiB write, then read back so no dirty lines remain)",
-                   "parallelism": "independent instance per GPU" if ws > 1 else "single GPU"},
+                   "parallelism": "independent instance per GPU" if ws > 1 else "single GPU",
+                   "path": args.path},
         "roofline": roofline,
         "path": {"algorithmic_bytes": path_bytes, "GBps": path_bytes / (ms_per_step * 1e-3) / 1e9,
                  "frac": path_bytes / (ms_per_step * 1e-3) / 1e9 / hbm,
@@ -366,8 +372,20 @@ def e2e_measure(g, h, wl, dev, stream, K, inst):
                 e[1].record(stream)
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    # the same two copies with no resampling between them: the host link's
+    # share of the step (the step cannot be faster than its copies)
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for a, b in cev:
+            a.record(stream)
+            wd.copy_(w_host, non_blocking=True)
+            out_host.copy_(out, non_blocking=True)
+            b.record(stream)
+    torch.cuda.synchronize()
+    cms = statistics.mean(a.elapsed_time(b) for a, b in cev)
     return {"value": N / (ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 8 * M, "d2h_bytes_per_step": 4 * N,
-            "ms_per_step": ms}
+            "ms_per_step": ms, "copies_only_ms_per_step": cms, "h2d_link_GBps": 8 * M / (cms * 1e-3) / 1e9,
+            "frac_of_copy_bound": cms / ms}
 
 
 def map_only(g, h, wl, dev, stream, K=50):

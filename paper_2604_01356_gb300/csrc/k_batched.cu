@@ -14,7 +14,8 @@
 //                     and Z_{N+1}; then key_i = ceil(Z_i S / Z_{N+1});
 //   D  map            segment-major: warp w takes a contiguous range of
 //                     segments and the samples whose keys fall in them (the
-//                     keys are sorted); each segment with samples is loaded
+//                     keys are sorted: one ballot over the next 32 keys finds
+//                     where a segment's samples end); each segment with samples is loaded
 //                     once, the next one travelling meanwhile, and its samples
 //                     are resolved from its exact prefixes - by a warp-wide
 //                     count when few samples fall in it, else by per-lane
@@ -248,17 +249,27 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
       for (int sc = sa; sc < sb && i < Nk; ++sc) {
         const bool last = sc == (int)nseg - 1;
         const u128 Pn = sm.pre[sc + 1];
-        long long ie = i;  // samples [i, ie) fall in segment sc
-        if (last) {
-          ie = Nk;
-        } else {
-          long long lo = i, hi = Nk;
-          while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if (!u128_lt(Pn, sm.key[mid])) lo = mid + 1;
-            else hi = mid;
+        // samples [i, ie) fall in segment sc: the first key above P_{sc+1}
+        // among the next 32 (one ballot; keys are sorted), a binary search
+        // beyond them only when more than 32 samples fall in the segment
+        const long long jl = i + lane;
+        u128 kl = {0ULL, 0ULL};  // key of sample i + lane, reused by the leaf
+        if (jl < Nk) kl = sm.key[jl];
+        long long ie = Nk;
+        if (!last) {
+          const unsigned above = __ballot_sync(0xFFFFFFFFu, jl >= Nk || u128_lt(Pn, kl));
+          if (above) {
+            ie = i + __ffs(above) - 1;
+            if (ie > Nk) ie = Nk;
+          } else {
+            long long lo = i + 32, hi = Nk;
+            while (lo < hi) {
+              const long long mid = (lo + hi) >> 1;
+              if (!u128_lt(Pn, sm.key[mid])) lo = mid + 1;
+              else hi = mid;
+            }
+            ie = lo;
           }
-          ie = lo;
         }
         if (ie == i) continue;
         Bits b[kSegV];
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
           for (long long j0 = i; j0 < ie; j0 += 32) {
             const long long j = j0 + lane;
             if (j < ie) {
-              const u128 key = sm.key[j];
+              const u128 key = j0 == i ? kl : sm.key[j];
               const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
               const unsigned long long Kq = ceil_units(rem, sh, Fs);
               int lo = 0, hi = kSeg;  // prefixes below K (non-decreasing)

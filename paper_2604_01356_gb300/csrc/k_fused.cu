@@ -50,6 +50,7 @@ extern "C" int rs_dbg_set_stamps(void* p) { return (int)cudaMemcpyToSymbol(gbr::
 #else
 #define GBR_STAMP_IF(cond, k) \
   do {                        \
+    (void)(cond);             \
   } while (0)
 #endif
 #define GBR_STAMP(k) GBR_STAMP_IF(threadIdx.x == 0, k)
@@ -189,54 +190,6 @@ static __device__ __noinline__ u128 spacing_ool(uint64_t word, const LogTab* tab
 // Owner CTA of segment t under the balanced split floor(nseg c / B).
 __device__ __forceinline__ int seg_owner(long long t, long long nseg, int B) {
   return (int)(((unsigned long long)(t + 1) * (unsigned)B - 1ULL) / (unsigned long long)nseg);
-}
-
-// Polls the slots of CTAs c_lo .. c_lo + n - 1 (n <= kXPerLane) together:
-// every poll issues all outstanding loads at once.
-constexpr int kXPerLane = kFusedMaxCtas / 32;
-__device__ __forceinline__ bool xget_many(const unsigned long long* base, int c_lo, int n, unsigned tag, int spin,
-                                          u128 (&val)[kXPerLane], unsigned (&ext)[kXPerLane]) {
-  unsigned pending = n > 0 ? (1u << n) - 1u : 0u;
-  int spins = 0;
-  while (pending) {
-    unsigned long long a0[kXPerLane], a1[kXPerLane], a2[kXPerLane];
-#pragma unroll
-    for (int k = 0; k < kXPerLane; ++k)
-      if ((pending >> k) & 1u) {
-        const unsigned long long* slot = base + kXSlotWords * (c_lo + k);
-        a0[k] = ld_relaxed_u64(slot);
-        a1[k] = ld_relaxed_u64(slot + 1);
-        a2[k] = ld_relaxed_u64(slot + 2);
-      }
-#pragma unroll
-    for (int k = 0; k < kXPerLane; ++k)
-      if (((pending >> k) & 1u) && (a0[k] & 0xFFFFu) == tag && (a1[k] & 0xFFFFu) == tag &&
-          (a2[k] & 0xFFFFu) == tag) {
-        const unsigned long long p0 = a0[k] >> 16, p1 = a1[k] >> 16, p2 = a2[k] >> 16;
-        val[k].lo = p0 | (p1 << 48);
-        val[k].hi = (p1 >> 16) | ((p2 & 0xFFFFFFFFULL) << 32);
-        ext[k] = (unsigned)(p2 >> 32);
-        pending &= ~(1u << k);
-      }
-    if (!pending) break;
-    if (++spins > spin) {
-#pragma unroll
-      for (int k = 0; k < kXPerLane; ++k)
-        if ((pending >> k) & 1u) {
-          val[k] = u128{0ULL, 0ULL};
-          ext[k] = 0;
-        }
-      return false;
-    }
-    __nanosleep(128);
-  }
-  return true;
-}
-// Warp-wide sum of a u128.
-__device__ __forceinline__ u128 warp_sum_v(u128 v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = u128_add(v, shfl_v(v, (threadIdx.x & 31) ^ o));
-  return v;
 }
 
 // Block-wide exclusive prefix of v (over lower thread indices) and total.
@@ -536,7 +489,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   __shared__ u128 s_S, s_zoff;
   __shared__ int s_Emax;
   __shared__ unsigned s_target;
-  __shared__ u128 s_ztot;
   __shared__ int s_flag_z, s_flag_inv;  // warp 0 -> last warp: Z_{N+1} ready; back: 1 / Z_{N+1} ready
   __shared__ unsigned long long s_lF[kLocalSegs];  // the CTA's segment records, when they fit
   __shared__ int s_lE[kLocalSegs];
