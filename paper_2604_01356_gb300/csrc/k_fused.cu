@@ -229,16 +229,14 @@ struct LeanSeg {
 __device__ __forceinline__ unsigned long long lean_pref(const unsigned long long* p, int j) {
   return p[(j & 15) * 32 + (j >> 4)];
 }
-// Number of elements whose exact prefix is below X.
+// Number of elements whose exact prefix is below X (the prefixes are
+// non-decreasing): nine fixed halving steps, no branch.
 __device__ __forceinline__ int lean_count(const unsigned long long* p, unsigned long long X) {
-  int lo = 0, hi = kSeg;
-#pragma unroll 1
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (lean_pref(p, mid) < X) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
+  static_assert(kSeg == 512, "nine steps");
+  int pos = 0;
+#pragma unroll
+  for (int step = kSeg / 2; step > 0; step >>= 1) pos += lean_pref(p, pos + step - 1) < X ? step : 0;
+  return pos + (lean_pref(p, pos) < X ? 1 : 0);
 }
 template <bool kVec>
 static __device__ __noinline__ int head_count_ool(const double* w, long long base, long long M, xf rem, int lane) {
@@ -487,6 +485,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   __shared__ int s_e[kFWarps], s_x[kFWarps];
   __shared__ xf s_c, s_invZ;
   __shared__ u128 s_S, s_zoff;
+  __shared__ u128 s_woff[kFWarps];  // spacing totals of the CTA's warps before each
   __shared__ int s_Emax;
   __shared__ unsigned s_target;
   __shared__ int s_flag_z, s_flag_inv;  // warp 0 -> last warp: Z_{N+1} ready; back: 1 / Z_{N+1} ready
@@ -548,15 +547,28 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   }
 
   // ---- phase 1a: the CTA's draws (Algorithm 1) -------------------------------
-  u128 ztot = {0ULL, 0ULL};
+  // Warp w < nW draws exactly the samples it maps below, [m0 + nsm w / nW,
+  // m0 + nsm (w+1) / nW), warp nW - 1 also the final draw N when this CTA
+  // holds it.  Each warp keeps its own exact running prefix (warp scans, no
+  // block barrier per tile); the warp totals are scanned once at the end, and
+  // the map adds the warp's offset.  With few draws per CTA the last warp
+  // takes none (it fetches the code of the scalar steps meanwhile).
+  const long long m0 = d0, m1 = d1 < a.N ? d1 : a.N;
+  const long long nsm = m1 > m0 ? m1 - m0 : 0;
+  const int nW = d1 - d0 > 4LL * kFThreads ? kFWarps : kFWarps - 1;
+  const long long g0 = warp < nW ? m0 + nsm * warp / nW : d1;
+  const long long g1 = warp < nW - 1 ? m0 + nsm * (warp + 1) / nW : d1;
+  const long long i1 = warp < nW ? m0 + nsm * (warp + 1) / nW : m1;
+  u128 ztot;
   {
-    const long long base = d0 & ~3LL;
+    u128 wrun = {0ULL, 0ULL};
+    const long long base = g0 & ~3LL;
 #pragma unroll 1
-    for (long long t0 = base; t0 < d1; t0 += 4LL * kFThreads) {
-      const long long k0 = t0 + 4LL * tid;
+    for (long long t0 = base; t0 < g1; t0 += 128) {
+      const long long k0 = t0 + 4LL * lane;
       u128 pre[4];
       u128 run = {0ULL, 0ULL};
-      const bool mine = k0 < d1 && k0 + 3 >= d0;
+      const bool mine = k0 < g1 && k0 + 3 >= g0;
       if (a.scheme == kSchemeMultinomial) {
         if (mine) {
           uint64_t words[4];
@@ -564,14 +576,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const long long k = k0 + q;
-            if (k >= d0 && k < d1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
+            if (k >= g0 && k < g1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
             pre[q] = run;
           }
         } else {
 #pragma unroll
           for (int q = 0; q < 4; ++q) pre[q] = run;
         }
-      } else if (__any_sync(0xFFFFFFFFu, mine)) {
+      } else {
         // strata points: every lane of the warp takes part (neighbour words)
         uint64_t words[4];
         philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
@@ -580,22 +592,30 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const long long k = k0 + q;
-          if (k >= d0 && k < d1) run = u128_add(run, f[q]);
+          if (k >= g0 && k < g1) run = u128_add(run, f[q]);
           pre[q] = run;
         }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) pre[q] = run;
       }
-      const BlockScan bs = block_scan(run, s_w);
-      const u128 excl = u128_add(bs.excl, ztot), tot = bs.tot;
+      const u128 incl = warp_incl_scan_v(run, lane);
+      const u128 excl = u128_add(wrun, u128_sub(incl, run));
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const long long k = k0 + q;
-        if (k >= d0 && k < d1 && k < a.N) a.Z[k] = u128_add(excl, pre[q]);
+        if (k >= g0 && k < g1 && k < a.N) a.Z[k] = u128_add(excl, pre[q]);
       }
-      ztot = u128_add(ztot, tot);
+      wrun = u128_add(wrun, shfl_v(incl, 31));
     }
+    if (lane == 0) s_w[warp] = wrun;
+    __syncthreads();
+    u128 before = {0ULL, 0ULL}, t = {0ULL, 0ULL};
+#pragma unroll
+    for (int i = 0; i < kFWarps; ++i) {
+      const u128 x = s_w[i];
+      if (i < warp) before = u128_add(before, x);
+      t = u128_add(t, x);
+    }
+    if (lane == 0) s_woff[warp] = before;  // read again by the map (s_w is reused before then)
+    ztot = t;
   }
   if (kVec && tid == 0)
     for (long long it = 1; it < n_it && it < kStages; ++it) issue(it);
@@ -758,11 +778,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   }
   GBR_STAMP(4);
 
-  // this warp's samples and the spacing prefixes of their first round, read
-  // before the exchange completes
-  const long long m0 = d0, m1 = d1 < a.N ? d1 : a.N;
-  const long long nsm = m1 > m0 ? m1 - m0 : 0;
-  const long long i0 = m0 + nsm * warp / kFWarps, i1 = m0 + nsm * (warp + 1) / kFWarps;
+  // this warp's samples (the draws it made) and the spacing prefixes of
+  // their first round, read before the exchange completes
+  const long long i0 = warp < nW ? g0 : m1;
   u128 z_first = {0ULL, 0ULL};
   if (i0 + lane < i1) z_first = u128{__ldcg(&a.Z[i0 + lane].lo), __ldcg(&a.Z[i0 + lane].hi)};
 
@@ -822,7 +840,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   cx.ge = (long long)Emax - a.kBS - kGridHead;
   cx.Emax = Emax;
   if (i1 > i0)
-    map_own<T, kVec>(w, a.M, a.seg, a.rel, a.nseg, a.Z, s_zoff, z_first, i0, i1, cx, s_cp, s_coarse, a.ncoarse,
+    map_own<T, kVec>(w, a.M, a.seg, a.rel, a.nseg, a.Z, u128_add(s_zoff, s_woff[warp]), z_first, i0, i1, cx, s_cp, s_coarse, a.ncoarse,
                      a.lgstride, B, s_buf, a.out);
 #ifdef GBR_PHASE_STAMPS
   __syncthreads();
