@@ -87,6 +87,16 @@ __device__ __forceinline__ u128 block_excl_scan(u128 v, u128* wsum, u128& total)
   return u128_add(off, u128_sub(incl, v));
 }
 
+// Number of the 512 non-decreasing entries p[0..511] below X: nine fixed
+// halving steps and a last compare, no branch.
+__device__ __forceinline__ int count_below(const unsigned long long* p, unsigned long long X) {
+  static_assert(kSeg == 512, "nine steps");
+  int pos = 0;
+#pragma unroll
+  for (int step = kSeg / 2; step > 0; step >>= 1) pos += p[pos + step - 1] < X ? step : 0;
+  return pos + (p[pos] < X ? 1 : 0);
+}
+
 __device__ __noinline__ void compute_c(xf* dst, u128 S, u128 Ztot) {
   *dst = xf_mul(xf_make(S.hi, S.lo, 0), recip_total(Ztot));
 }
@@ -328,12 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
               const u128 key = j0 == i ? kl : sm.key[j];
               const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
               const unsigned long long Kq = ceil_units(rem, sh, Fs);
-              int lo = 0, hi = kSeg;  // prefixes below K (non-decreasing)
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (sp[mid] < Kq) lo = mid + 1;
-                else hi = mid;
-              }
+              const int lo = count_below(sp, Kq);
               const int jj = lo < len ? lo : len - 1;
               long long idx = (long long)sc * kSeg + jj;
               if (idx > Mk - 1) idx = Mk - 1;

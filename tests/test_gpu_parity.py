@@ -331,6 +331,31 @@ def test_fused_equals_multikernel(g, h, prec, M, N):
     assert np.array_equal(host(a), host(b))
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("which", ["all_few", "mixed", "all_many"])
+def test_fused_draw_split_modes(g, h, prec, which):
+    """The cooperative launch splits a CTA's draws over 15 warps when it holds
+    at most 2048 of them, else over all 16 with per-warp prefixes.  N = 2048 B - 1
+    (every CTA exactly 2048 draws), N = 2048 B (one CTA 2049: both modes in one
+    launch) and N = 600,000 (every CTA above 2048) against the multi-kernel path."""
+    B = torch.cuda.get_device_properties(0).multi_processor_count
+    N = {"all_few": 2048 * B - 1, "mixed": 2048 * B, "all_many": 600_000}[which]
+    M = N + 12_345
+    w = workloads.weights_lognormal(M, 2.0, seed=N)
+    if prec == "f32":
+        w = w.astype(np.float32)
+    p = g.RS_F32_COMP if prec == "f32" else g.RS_F64
+    wd = dev(w)
+    a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    b = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, N, 17, 3, a, None, g.opts(prec=p))
+    g.rs_resample_w(h.h, wd, M, N, 17, 3, b, None, g.opts(prec=p, debug_flags=2))
+    assert h.status() == g.RS_OK
+    ra = host(a)
+    assert np.array_equal(ra, host(b))
+    assert ra.min() >= 0 and ra.max() < M and np.all(np.diff(ra) >= 0)
+
+
 @pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
 def test_fused_equals_multikernel_adversarial(g, h, kind):
     M, N = 7 * 4096 + 3, 5000

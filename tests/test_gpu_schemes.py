@@ -69,7 +69,8 @@ def test_scheme_points_f32(g, h, scheme):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-@pytest.mark.parametrize("M,N", [(1, 3), (513, 1000), (9 * 4096 + 5, 4097), (1_000_003, 300_001), (200_000, 200_000)])
+@pytest.mark.parametrize("M,N", [(1, 3), (513, 1000), (9 * 4096 + 5, 4097), (1_000_003, 300_001), (200_000, 200_000),
+                                 (600_001, 600_000)])
 def test_scheme_resample_w_fused_and_multikernel(g, h, scheme, M, N):
     w = workloads.weights_lognormal(M, 2.0, seed=M + 7)
     r_ref, W_ref, U_ref = oracle.resample_scheme(w, N, 99, scheme)
