@@ -357,28 +357,59 @@ __device__ __forceinline__ bool u128_lt(const u128& a, const u128& b) {
   return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 // key = ceil(Z_i * c) with c = S_grid / Z_{N+1}: U_i * S in grid units,
-// rounded up (so that "prefix >= key" is "W >= U").
+// rounded up (so that "prefix >= key" is "W >= U").  Exact: the 256-bit
+// product of c's mantissa and Z_i, shifted by c's (call-uniform) exponent,
+// plus one when any bit below the unit is set.
 __device__ __forceinline__ u128 map_key(const xf& c, u128 z) {
-  const xf kx = xf_mul_u128(c, z);
-  u128 key = {0ULL, 0ULL};
-  if (!xf_zero(kx)) {
-    uint64_t kh = kx.hi, kl = kx.lo;
-    if (kx.e >= 0) {
-      shl128(kh, kl, kx.e > 1 ? 1 : (int)kx.e);  // key <= S < 2^126: e <= 1
-    } else {
-      const int r = kx.e < -127 ? 128 : (int)(-kx.e);
-      uint64_t th = kh, tl = kl;
-      shr128(th, tl, r);
-      uint64_t bh = th, bl = tl;
-      shl128(bh, bl, r < 128 ? r : 0);
-      const bool frac = r >= 128 ? true : (bh != kh || bl != kl);
-      kh = th;
-      kl = tl + (frac ? 1ULL : 0ULL);
-      if (kl < tl) ++kh;
-    }
-    key = u128{kl, kh};
+  if (xf_zero(c) || (z.hi | z.lo) == 0) return u128{0ULL, 0ULL};
+  uint64_t p0h, p0l, p1h, p1l, p2h, p2l, p3h, p3l;
+  mul64(c.lo, z.lo, p0h, p0l);
+  mul64(c.lo, z.hi, p1h, p1l);
+  mul64(c.hi, z.lo, p2h, p2l);
+  mul64(c.hi, z.hi, p3h, p3l);
+  // P = w3:w2:w1:w0
+  const uint64_t w0 = p0l;
+  uint64_t w1 = p0h + p1l;
+  uint64_t c1 = w1 < p0h;
+  w1 += p2l;
+  c1 += w1 < p2l;
+  uint64_t w2 = p3l + p1h;
+  uint64_t c2 = w2 < p3l;
+  w2 += p2h;
+  c2 += w2 < p2h;
+  w2 += c1;
+  c2 += w2 < c1;
+  const uint64_t w3 = p3h + c2;
+  if (c.e >= 0) {  // key = P << e, below 2^126: only small products (e <= 1)
+    const int e = c.e > 2 ? 2 : (int)c.e;
+    uint64_t hi = w1, lo = w0;
+    shl128(hi, lo, e);
+    return u128{lo, hi};
   }
-  return key;
+  const long long k = -c.e;  // key = ceil(P / 2^k)
+  if (k >= 256) return u128{1ULL, 0ULL};
+  const int j = (int)(k >> 6), b = (int)(k & 63);
+  // the 192 bits from word j up, and whether any bit below bit k is set
+  uint64_t a0, a1, a2;
+  bool frac;
+  if (j == 0) {
+    a0 = w0; a1 = w1; a2 = w2;
+    frac = (w0 & ((1ULL << b) - 1ULL)) != 0;
+  } else if (j == 1) {
+    a0 = w1; a1 = w2; a2 = w3;
+    frac = w0 != 0 || (w1 & ((1ULL << b) - 1ULL)) != 0;
+  } else if (j == 2) {
+    a0 = w2; a1 = w3; a2 = 0;
+    frac = (w0 | w1) != 0 || (w2 & ((1ULL << b) - 1ULL)) != 0;
+  } else {
+    a0 = w3; a1 = 0; a2 = 0;
+    frac = (w0 | w1 | w2) != 0 || (w3 & ((1ULL << b) - 1ULL)) != 0;
+  }
+  uint64_t lo = b ? (a0 >> b) | (a1 << (64 - b)) : a0;
+  uint64_t hi = b ? (a1 >> b) | (a2 << (64 - b)) : a1;
+  lo += frac ? 1ULL : 0ULL;
+  if (frac && lo == 0) ++hi;
+  return u128{lo, hi};
 }
 
 // K = ceil(rem / 2^sh) clamped to [1, F]: the segment-grid target of a key
