@@ -403,6 +403,18 @@ __device__ __forceinline__ void map_own(const T* __restrict__ w, long long M, co
     long long s_me = c.cur;
     u128 P_me = c.Ps;
     unsigned need = __ballot_sync(0xFFFFFFFFu, valid && !in_cur);
+    if (!need && !c.head) {
+      // every sample of the round lies in the current (non-head) segment:
+      // the in-segment decision directly, without the grouping below
+      if (valid) {
+        const u128 rem = u128_lt(c.Ps, key) ? u128_sub(key, c.Ps) : u128{0ULL, 0ULL};
+        const int cnt = lean_count(cx.s_pref + warp * kSeg, ceil_units(rem, c.sh, c.F));
+        long long rr = c.cur * kSeg + (cnt < c.len ? cnt : c.len - 1);
+        if (rr > M - 1) rr = M - 1;
+        out[i] = (int)rr;
+      }
+      continue;
+    }
     if (need) {
       // coarse block: the last j with coarse_j < key (coarse_0 = 0 < key)
       long long j_me = 0;

@@ -93,6 +93,15 @@ __device__ __forceinline__ f3 f64_split(unsigned long long b) {
   return {h, m, t};
 }
 
+// binary32 pair plus one binary32: two-sum of the high parts, the low part
+// folded in, renormalised.  The only rounding is that of the two low parts'
+// sum (below 2^-24 of it); half the operations of a pair-plus-pair addition.
+__device__ __forceinline__ df df_add_f(df a, float b) {
+  df s = df_two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return df_fast_two_sum(s.hi, s.lo);
+}
+
 // exp(x) for x = s + e + a + b + c + d <= 0 (s, e an exact two-sum, the
 // others small binary32 terms), as binary64 bits.  The reduction consumes
 // the terms one by one, so only the small remainder r is ever rounded
@@ -107,14 +116,14 @@ __device__ __forceinline__ unsigned long long exp_neg_bits(float s, float e, flo
   const int n = __float2int_rn(s * kInvL);  // |n| < 2^17: n L1 exact
   const float fn = (float)n;
   df r = df_two_sum(s - fn * L1, e);  // the first difference is exact (Sterbenz)
-  r = df_add(r, df{a, 0.0f});
-  r = df_add(r, df{b, 0.0f});
-  r = df_add(r, df{c, 0.0f});
-  r = df_add(r, df{d, 0.0f});
+  r = df_add_f(r, a);
+  r = df_add_f(r, b);
+  r = df_add_f(r, c);
+  r = df_add_f(r, d);
   const float p = fn * L2;
   const float pe = fmaf(fn, L2, -p);
   r = df_add(r, df{-p, -pe});
-  r = df_add(r, df{-fn * L3, 0.0f});
+  r = df_add_f(r, -fn * L3);
   // e^r = 1 + r + r^2 (1/2 + q), q = r/6 + r^2/24 + r^3/120 + r^4/720 (binary32 suffices)
   const float rh = r.hi;
   const float q = rh * (1.0f / 6.0f + rh * (1.0f / 24.0f + rh * (1.0f / 120.0f + rh * (1.0f / 720.0f))));
