@@ -13,6 +13,7 @@ the data path).  L2 is flushed (256 MiB write, read back) before every timed ste
 each step is timed with CUDA events on its stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--path fused|multikernel] [--no-extras] [--no-cpu-baseline]
 """
 import argparse
 import hashlib

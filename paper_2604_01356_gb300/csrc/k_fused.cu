@@ -5,18 +5,21 @@
 // a contiguous range of the N+1 draws (and of the N samples):
 //
 //   phase 1  the CTA's draws: Philox, spacings -log v on the 2^-88 grid and
-//            their exact in-CTA inclusive prefixes (Algorithm 1);
-//            the CTA's segments: streamed into shared memory by bulk async
-//            copies (TMA engine, a ring of stages completed on mbarriers),
-//            exact segment sums (one warp per segment).
+//            their exact inclusive prefixes (Algorithm 1), each warp over
+//            the draws of the samples it maps later, plus the warps'
+//            offsets; the CTA's segments: streamed into shared memory by bulk
+//            async copies (TMA engine, a ring of stages completed on
+//            mbarriers), exact segment sums (one warp per segment).
 //   exchange 1  every CTA publishes its largest segment exponent and its
-//            spacing total; every CTA reads all of them (release/acquire
-//            flags, bounded waits): Emax, Z_{N+1} and the CTA's own spacing
-//            offset follow.
+//            spacing total; every CTA reads all of them (tagged words,
+//            bounded waits): Emax, Z_{N+1} and the CTA's own spacing offset
+//            follow.
 //   phase 2  the CTA's segment sums on the global grid (unit fixed by
 //            Emax), exact prefixes relative to the CTA range, the CTA total.
-//   exchange 2  every CTA publishes its total and reads all of them: the
-//            CTA prefixes and S.
+//   exchange 2  every CTA publishes its total and reads all of them
+//            (release and acquire fences around it: the range prefixes and
+//            segment records of other CTAs are read next): the CTA prefixes
+//            and S.
 //   phase 3  the map of the CTA's own samples: key ceil(U_i S), the owner
 //            CTA of the key by binary search over the CTA prefixes and a
 //            coarse index in shared memory, the segment among 32 prefixes,
@@ -500,7 +503,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   __shared__ u128 s_woff[kFWarps];  // spacing totals of the CTA's warps before each
   __shared__ int s_Emax;
   __shared__ unsigned s_target;
-  __shared__ int s_flag_z, s_flag_inv;  // warp 0 -> last warp: Z_{N+1} ready; back: 1 / Z_{N+1} ready
   __shared__ unsigned long long s_lF[kLocalSegs];  // the CTA's segment records, when they fit
   __shared__ int s_lE[kLocalSegs];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -517,8 +519,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   const bool local = s1 - s0 <= kLocalSegs;
 
   if (tid == 0) {
-    s_flag_z = 0;
-    s_flag_inv = 0;
     s_target = __ldcg(a.xch) + 1u;  // this call's epoch
     if (kVec) {
       for (int s = 0; s < kStages; ++s) {

@@ -185,6 +185,38 @@ def test_resample_w_f64(g, h, M, N):
     assert Wg[-1] == 1.0 and np.all(np.abs(Wg - W_ref) <= REL_F64 * W_ref + 1e-300)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_resample_w_unaligned_weights(g, h, prec):
+    """Weights starting one element past a 16-byte boundary (no bulk copies:
+    the cooperative launch reads them with plain loads), ragged M, against
+    the multi-kernel path and the oracle; N = 0 is a no-op."""
+    M, N = 300_001, 5000
+    w = workloads.weights_lognormal(M, 2.0, seed=71)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    if prec == "f32":
+        w = w.astype(np.float32)
+    p = g.RS_F32_COMP if prec == "f32" else g.RS_F64
+    buf = torch.zeros(M + 1, dtype=dt, device="cuda")
+    buf[1:] = torch.from_numpy(w).cuda()
+    wd = buf[1:]
+    assert wd.data_ptr() % 16 != 0
+    a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    b = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, N, 5, 1, a, None, g.opts(prec=p))
+    g.rs_resample_w(h.h, wd, M, N, 5, 1, b, None, g.opts(prec=p, debug_flags=2))
+    assert h.status() == g.RS_OK
+    ra = host(a)
+    assert np.array_equal(ra, host(b))
+    r_ref, W_ref, U_ref = oracle.resample(w, N, 5, instance=1, single=prec == "f32")
+    if prec == "f32":
+        assert_boundary_only(ra, r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+    else:
+        assert_boundary_only(ra, r_ref, W_ref, U_ref, rel=REL_F64)
+    z = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, 0, 5, 1, z, None, g.opts(prec=p))
+    assert h.status() == g.RS_OK and int(host(z)[0]) == -7
+
+
 @pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
 def test_resample_w_adversarial(g, h, kind):
     M, N = 5 * 4096 + 17, 4096
