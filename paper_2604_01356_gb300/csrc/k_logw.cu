@@ -130,7 +130,7 @@ __device__ __forceinline__ unsigned long long exp_neg_bits(float s, float e, flo
   const df r2 = df_mul(r, r);
   df ex = df_add(df_mul_f(r2, q), df{r2.hi * 0.5f, r2.lo * 0.5f});
   ex = df_add(ex, r);
-  ex = df_add(df{1.0f, 0.0f}, ex);
+  ex = df_add_f(ex, 1.0f);
   const int k = n >> 6, j = n & 63;
   const df t = {T[j].x, T[j].y};
   const df v = df_mul(t, ex);  // in [0.99, 2.01]
