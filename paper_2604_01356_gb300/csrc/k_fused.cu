@@ -568,8 +568,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   const long long m0 = d0, m1 = d1 < a.N ? d1 : a.N;
   const long long nsm = m1 > m0 ? m1 - m0 : 0;
   const int nW = d1 - d0 > 4LL * kFThreads ? kFWarps : kFWarps - 1;
-  const long long g0 = warp < nW ? m0 + nsm * warp / nW : d1;
-  const long long g1 = warp < nW - 1 ? m0 + nsm * (warp + 1) / nW : d1;
+  const long long g0 = warp < nW ? m0 + nsm * warp / nW : 0;  // [0, 0): no draws
+  const long long g1 = warp < nW - 1 ? m0 + nsm * (warp + 1) / nW : (warp < nW ? d1 : 0);
   const long long i1 = warp < nW ? m0 + nsm * (warp + 1) / nW : m1;
   u128 ztot;
   {
