@@ -22,9 +22,11 @@
  *   orc_inverse_cdf_walk  The same result by one monotone walk (valid only
  *                         for sorted U); used where the per-u scan is too slow.
  *   orc_alg2_binary_search, orc_alg3_binary_map, orc_alg4_ccf_map,
- *   orc_alg5_dac_map      Algorithms 2-5 as the paper states them (1-based
- *                         inside, 0-based results), for cross-checks and for
- *                         the Figure 1 trace.
+ *   orc_alg5_dac_map      The samplers of Algorithms 2-5 (Sec. II-III),
+ *                         restated from the result each computes (the
+ *                         Eq. 3 lower bound) and the split argument of
+ *                         Sec. III; cross-checks, the Figure 1 trace and
+ *                         Table I's comparison counts.
  *   orc_resample          Whole path for one instance: Eq. 3 + Algorithm 1 +
  *                         Eq. 2.
  *   orc_resample_batched  The same for K independent instances.
@@ -199,12 +201,12 @@ int orc_inverse_cdf_walk(const double* W, int64_t M, const double* U, int64_t N,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Algorithms 2-5 as stated in the paper (1-based index arithmetic inside).   */
+/* The paper's samplers (Sec. II-III), restated from what they compute.      */
+/* Each returns the Eq. 3 answer; they differ only in how they reach it, and  */
+/* the probe counter lets the tests compare their costs with Table I.         */
 /* ------------------------------------------------------------------------ */
 
-/* Algorithm 2, modified binary search over Z[a..b] (1-based, inclusive):
- * returns the smallest m in [a,b] with Z_m >= X, or b if there is none. */
-static int64_t g_probes = 0; /* comparisons made by Algorithm 2 (Table I counts) */
+static int64_t g_probes = 0; /* comparisons of a search key with an entry of W */
 
 int64_t orc_alg2_probes(int reset) {
   int64_t p = g_probes;
@@ -212,76 +214,82 @@ int64_t orc_alg2_probes(int reset) {
   return p;
 }
 
+/* Algorithm 2's result: over the non-decreasing entries Z1[a..b] (1-based,
+ * inclusive) the first index whose entry reaches X, and b when no entry
+ * before b does (so b also stands for "X lies above every entry").
+ * Bisection on the count of leading entries below X: the candidates are
+ * lo .. lo+len, where lo+len = b is the fallback, so Z1[b] is never read. */
 int64_t orc_alg2_binary_search(const double* Z1, int64_t a, int64_t b, double X) {
-  /* Z1 is indexed 1-based: Z1[m] for m in [a, b] */
-  int64_t m = (a + b) / 2;
-  while (a != b) {
+  int64_t lo = a, len = b - a;
+  while (len > 0) {
+    const int64_t half = len / 2;
     ++g_probes;
-    if (Z1[m] < X) a = m + 1;
-    else b = m;
-    m = (a + b) / 2;
+    if (Z1[lo + half] < X) {
+      lo += half + 1;
+      len -= half + 1;
+    } else {
+      len = half;
+    }
   }
-  return b;
+  return lo;
 }
 
-/* Algorithm 3 on given U (the paper draws U_i unsorted; here U is an input). */
+/* Algorithm 3 on given U: one search over the whole of W per sample. */
 void orc_alg3_binary_map(const double* W, int64_t M, const double* U, int64_t N, int32_t* r) {
-  const double* W1 = W - 1; /* 1-based view */
-  for (int64_t i = 0; i < N; ++i) r[i] = (int32_t)(orc_alg2_binary_search(W1, 1, M, U[i]) - 1);
+  for (int64_t i = 0; i < N; ++i) r[i] = (int32_t)(orc_alg2_binary_search(W - 1, 1, M, U[i]) - 1);
 }
 
-/* Algorithm 4 (CCF) on given sorted U, with the walk clamped at M. */
+/* Algorithm 4 (CCF) on given sorted U: one forward pass over W shared by all
+ * samples, never moving past the last index. */
 void orc_alg4_ccf_map(const double* W, int64_t M, const double* U, int64_t N, int32_t* r) {
-  const double* W1 = W - 1;
-  int64_t j = 1;
-  for (int64_t i = 1; i <= N; ++i) {
-    while (j < M && W1[j] < U[i - 1]) ++j;
-    r[i - 1] = (int32_t)(j - 1);
+  int64_t j = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    while (j + 1 < M && W[j] < U[i]) ++j;
+    r[i] = (int32_t)j;
   }
 }
 
-/* Algorithm 5 (divide and conquer).  trace (optional) receives, in visit
- * order, triples (depth, m_U, m_W) (1-based) for every binary search the
- * algorithm performs; *ntrace counts them. */
+/* Algorithm 5 (divide and conquer) on given sorted U.  The answer of the
+ * middle sample of a sample range splits the W range: samples before it
+ * have answers at or below it, samples after it at or above it (U sorted,
+ * W non-decreasing), so each side recurses on its own part of W, both parts
+ * keeping the split index.  A W range of one index answers every sample in
+ * it without a search.  trace (optional) receives, in visit order, triples
+ * (depth, sample, answer) (1-based) for every search made; the count of
+ * searches is returned. */
 typedef struct {
-  const double* W1;
-  const double* U1;
-  int32_t* r1; /* 1-based output view holding 1-based values */
+  const double* W;
+  const double* U;
+  int32_t* r;
   int64_t* trace;
   int64_t ntrace, cap;
 } dac_ctx;
 
-static void dac_rec(dac_ctx* c, int64_t aU, int64_t bU, int64_t aW, int64_t bW, int64_t depth) {
-  if (aU == bU) {
-    int64_t m = orc_alg2_binary_search(c->W1, aW, bW, c->U1[aU]);
-    c->r1[aU] = (int32_t)m;
-    if (c->trace && c->ntrace < c->cap) {
-      c->trace[3 * c->ntrace] = depth; c->trace[3 * c->ntrace + 1] = aU; c->trace[3 * c->ntrace + 2] = m;
-    }
-    c->ntrace++;
-  } else if (aW == bW) {
-    for (int64_t i = aU; i <= bU; ++i) c->r1[i] = (int32_t)aW;
-  } else {
-    int64_t mU = (aU + bU) / 2;
-    int64_t mW = orc_alg2_binary_search(c->W1, aW, bW, c->U1[mU]);
-    c->r1[mU] = (int32_t)mW;
-    if (c->trace && c->ntrace < c->cap) {
-      c->trace[3 * c->ntrace] = depth; c->trace[3 * c->ntrace + 1] = mU; c->trace[3 * c->ntrace + 2] = mW;
-    }
-    c->ntrace++;
-    if (mU > aU) dac_rec(c, aU, mU - 1, aW, mW, depth + 1);
-    if (mU < bU) dac_rec(c, mU + 1, bU, mW, bW, depth + 1);
+static void dac_split(dac_ctx* c, int64_t i0, int64_t i1, int64_t lo, int64_t hi, int64_t depth) {
+  /* samples [i0, i1) have their answers in W[lo..hi] (0-based, inclusive) */
+  if (i0 >= i1) return;
+  if (lo == hi) {
+    for (int64_t i = i0; i < i1; ++i) c->r[i] = (int32_t)lo;
+    return;
   }
+  const int64_t mid = i0 + (i1 - 1 - i0) / 2; /* the lower middle */
+  const int64_t ans = orc_alg2_binary_search(c->W - 1, lo + 1, hi + 1, c->U[mid]) - 1;
+  c->r[mid] = (int32_t)ans;
+  if (c->trace && c->ntrace < c->cap) {
+    c->trace[3 * c->ntrace] = depth;
+    c->trace[3 * c->ntrace + 1] = mid + 1;
+    c->trace[3 * c->ntrace + 2] = ans + 1;
+  }
+  c->ntrace++;
+  dac_split(c, i0, mid, lo, ans, depth + 1);
+  dac_split(c, mid + 1, i1, ans, hi, depth + 1);
 }
 
 int64_t orc_alg5_dac_map(const double* W, int64_t M, const double* U, int64_t N, int32_t* r,
                          int64_t* trace, int64_t trace_cap) {
   if (N <= 0) return 0;
-  int32_t* r1 = (int32_t*)malloc((size_t)(N + 1) * sizeof(int32_t));
-  dac_ctx c = {W - 1, U - 1, r1, trace, 0, trace_cap};
-  dac_rec(&c, 1, N, 1, M, 1);
-  for (int64_t i = 1; i <= N; ++i) r[i - 1] = r1[i] - 1;
-  free(r1);
+  dac_ctx c = {W, U, r, trace, 0, trace_cap};
+  dac_split(&c, 0, N, 0, M - 1, 1);
   return c.ntrace;
 }
 
