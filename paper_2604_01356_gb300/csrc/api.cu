@@ -775,7 +775,8 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
     RS_TRACE(h, "batched", st);
     RS_CK(h, launch_batched_f32(static_cast<const float*>(w), reinterpret_cast<const long long*>(w_off),
                                 reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, threads, leaf,
-                                out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme));
+                                out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme,
+                                static_cast<const LogTab*>(h->logtab)));
   }
   return RS_OK;
 }

@@ -148,7 +148,7 @@ constexpr int kSortMax = 16384;   // batches up to this size are ordered by M_k 
 cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cudaStream_t st);
 cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                                unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st, int scheme = 0);
+                               int* status, cudaStream_t st, int scheme, const LogTab* tab);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

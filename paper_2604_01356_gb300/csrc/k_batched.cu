@@ -66,6 +66,7 @@ struct BatchSmem {
   xf c;
   int emax_w[kWarps];
   int item;
+  LogTab tab;  // logarithm table of the spacings
 };
 
 // Exclusive block scan of one u128 per thread; also returns the total.
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
                                                           const int* __restrict__ order, int K,
                                                           unsigned long long seed, int leaf_T,
                                                           int* __restrict__ out, unsigned* queue, int* status,
-                                                          int scheme) {
+                                                          int scheme, const LogTab* __restrict__ tab) {
   using Tr = FixedTraits<float>;
   using Bits = Tr::Bits;
   constexpr int kWarps = kThreads / 32;
@@ -119,6 +120,10 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
   BatchSmem<kWarps>& sm = *reinterpret_cast<BatchSmem<kWarps>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
+  for (int i = tid; i < 129; i += kThreads) {
+    sm.tab.nlogc[i] = tab->nlogc[i];
+    sm.tab.invc[i] = tab->invc[i];
+  }
   bool first = true;
   GBR_BSTAMP(true, 0);
   while (true) {
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
       uint64_t wd[4];
       philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
       u128 f[4];
-      block_spacings<true>(scheme, k0, ndraw, seed, (unsigned long long)k, wd, nullptr, f);
+      block_spacings<true>(scheme, k0, ndraw, seed, (unsigned long long)k, wd, &sm.tab, f);
       u128 run = {0ULL, 0ULL}, inc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
 template <int kThreads>
 static cudaError_t batched_t(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                              unsigned long long seed, int leaf_T, int* out, unsigned* queue, int* status,
-                             cudaStream_t st, int scheme) {
+                             cudaStream_t st, int scheme, const LogTab* tab) {
   const size_t smem = sizeof(BatchSmem<kThreads / 32>);
   cudaError_t e = cudaFuncSetAttribute(k_batched_f32<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -370,18 +375,18 @@ static cudaError_t batched_t(const float* w, const long long* w_off, const long 
   if (blocks > K) blocks = K;
   if (blocks < 1) blocks = 1;
   k_batched_f32<kThreads><<<(unsigned)blocks, kThreads, smem, st>>>(w, w_off, r_off, order, K, seed, leaf_T, out,
-                                                                     queue, status, scheme);
+                                                                     queue, status, scheme, tab);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
                                unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st, int scheme) {
+                               int* status, cudaStream_t st, int scheme, const LogTab* tab) {
   if (K <= 0) return cudaSuccess;
   switch (threads) {
-    case 128: return batched_t<128>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
-    case 512: return batched_t<512>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
-    default: return batched_t<256>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme);
+    case 128: return batched_t<128>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
+    case 512: return batched_t<512>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
+    default: return batched_t<256>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
   }
 }
 

@@ -69,6 +69,7 @@ constexpr int kStageBytes = 64 * 1024;     // 16 binary64 or 32 binary32 segment
 static_assert(kStageBytes < (1 << 20), "an mbarrier phase counts fewer than 2^20 bytes");
 constexpr int kCoarseMax = 1024;           // coarse-index entries in shared memory
 constexpr int kTmaSpin = 1 << 20;          // safety bound of the copy-completion waits
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
 struct FusedArgs {
   const void* w;
@@ -84,7 +85,8 @@ struct FusedArgs {
   int* status;
   int spin;
   bool withhold_first;
-  const LogTab* tab;  // logarithm table (binary64 draws)
+  const LogTab* tab;  // logarithm table of the spacings
+  bool few;           // one warp makes the draws while fifteen stream
   int kBS;
   int* out;
   int scheme;         // uniforms: Algorithm 1, stratified or systematic points
@@ -188,6 +190,112 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
 template <bool F32>
 static __device__ __noinline__ u128 spacing_ool(uint64_t word, const LogTab* tab) {
   return spacing_fixed<F32>(word, tab);
+}
+
+// The exact segment sum of seg_sum_bits for a segment staged in shared memory
+// (lane l's elements in the 16-byte pieces at 16 l + 512 q), in two passes
+// over shared memory (largest exponent field, then the fixed-point sum) so
+// that the segment is never held in registers; the rare segment with a sign
+// bit or a non-finite weight takes the register path.  The sum is an exact
+// integer sum, so the result is that of seg_sum_bits.
+template <typename T>
+__device__ __forceinline__ void seg_sum_smem(const unsigned char* src, int lane, int* status, uint64_t& F,
+                                             uint32_t& E) {
+  using Tr = FixedTraits<T>;
+  using Bits = typename Tr::Bits;
+  constexpr int kPer = 16 / (int)sizeof(T);  // elements per 16-byte piece
+  uint32_t tmax = 0;
+#pragma unroll
+  for (int q = 0; q < kSegV / kPer; ++q) {
+    const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * lane + 512 * q);
+    if (sizeof(T) == 4) tmax = max(tmax, max(max(v.x >> 23, v.y >> 23), max(v.z >> 23, v.w >> 23)));
+    else tmax = max(tmax, max(v.y >> 20, v.w >> 20));  // sign and exponent fields
+  }
+  tmax = __reduce_max_sync(kFull, tmax);
+  constexpr uint32_t kTopInf = sizeof(T) == 8 ? 0x7FFu : 0xFFu;
+  if (tmax < kTopInf) {
+    E = tmax > 1u ? tmax : 1u;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int q = 0; q < kSegV / kPer; ++q) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * lane + 512 * q);
+      if (sizeof(T) == 4) {
+        sum += Tr::fixed((Bits)v.x, E) + Tr::fixed((Bits)v.y, E) + Tr::fixed((Bits)v.z, E) + Tr::fixed((Bits)v.w, E);
+      } else {
+        sum += fixed64_valid(((uint64_t)v.y << 32) | v.x, E) + fixed64_valid(((uint64_t)v.w << 32) | v.z, E);
+      }
+    }
+    F = warp_sum_u64(sum);
+  } else {
+    Bits b[kSegV];
+#pragma unroll
+    for (int q = 0; q < kSegV / kPer; ++q) {
+      const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * lane + 512 * q);
+      if (sizeof(T) == 4) {
+        b[4 * q] = (Bits)v.x;
+        b[4 * q + 1] = (Bits)v.y;
+        b[4 * q + 2] = (Bits)v.z;
+        b[4 * q + 3] = (Bits)v.w;
+      } else {
+        b[2 * q] = (Bits)(((uint64_t)v.y << 32) | v.x);
+        b[2 * q + 1] = (Bits)(((uint64_t)v.w << 32) | v.z);
+      }
+    }
+    seg_sum_bits<T>(b, lane, status, F, E);
+  }
+}
+
+// The draws [g0, g1) of the stream by one warp (Algorithm 1's spacings, or
+// the strata spacings): their exact inclusive prefixes relative to g0 are
+// stored as Z[k] for k < N.  Returns the warp's total (every lane).
+template <bool F32>
+__device__ __forceinline__ u128 draw_range(const FusedArgs& a, long long g0, long long g1, const LogTab* tab,
+                                           int lane) {
+  u128 wrun = {0ULL, 0ULL};
+  const long long base = g0 & ~3LL;
+#pragma unroll 1
+  for (long long t0 = base; t0 < g1; t0 += 128) {
+    const long long k0 = t0 + 4LL * lane;
+    u128 pre[4];
+    u128 run = {0ULL, 0ULL};
+    const bool mine = k0 < g1 && k0 + 3 >= g0;
+    if (a.scheme == kSchemeMultinomial) {
+      if (mine) {
+        uint64_t words[4];
+        philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const long long k = k0 + q;
+          if (k >= g0 && k < g1) run = u128_add(run, spacing_ool<F32>(words[q], tab));
+          pre[q] = run;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pre[q] = run;
+      }
+    } else {
+      // strata points: every lane of the warp takes part (neighbour words)
+      uint64_t words[4];
+      philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
+      u128 f[4];
+      block_spacings<F32>(a.scheme, k0, a.ndraw, a.seed, a.inst, words, tab, f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long k = k0 + q;
+        if (k >= g0 && k < g1) run = u128_add(run, f[q]);
+        pre[q] = run;
+      }
+    }
+    const u128 incl = warp_incl_scan_v(run, lane);
+    const u128 excl = u128_add(wrun, u128_sub(incl, run));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long k = k0 + q;
+      if (k >= g0 && k < g1 && k < a.N) a.Z[k] = u128_add(excl, pre[q]);
+    }
+    wrun = u128_add(wrun, shfl_v(incl, 31));
+  }
+  return wrun;
 }
 
 // Owner CTA of segment t under the balanced split floor(nseg c / B).
@@ -491,8 +599,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   constexpr bool F32 = sizeof(T) == 4;
   using Bits = typename FixedTraits<T>::Bits;
   constexpr int kSegBytes = kSeg * (int)sizeof(T);
-  constexpr int kStageSegs = kStageBytes / kSegBytes;
-  constexpr int kSegsPerWarp = kStageSegs / kFWarps;
+  constexpr int kSegsPerWarp = kStageBytes / kSegBytes / kFWarps;  // stage segments per streaming warp
   extern __shared__ __align__(128) unsigned char s_dyn[];
   __shared__ LogTab tab;
   __shared__ u128 s_w[kFWarps];
@@ -501,7 +608,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   __shared__ xf s_c, s_invZ;
   __shared__ u128 s_S, s_zoff;
   __shared__ u128 s_woff[kFWarps];  // spacing totals of the CTA's warps before each
-  __shared__ int s_Emax;
+  __shared__ u128 s_wz[kFWarps];    // the warps' spacing totals
+  __shared__ int s_Emax, s_abort;
   __shared__ unsigned s_target;
   __shared__ unsigned long long s_lF[kLocalSegs];  // the CTA's segment records, when they fit
   __shared__ int s_lE[kLocalSegs];
@@ -511,35 +619,19 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   unsigned long long* x1 = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(a.xch) + 256);
   unsigned long long* x2 = x1 + kXSlotWords * kFusedMaxCtas;
 
-  // ranges of this CTA
+  // ranges of this CTA; with few draws warp 15 makes them all while the
+  // other fifteen stream the weights
+  const int nSW = a.few ? kFWarps - 1 : kFWarps;  // streaming warps
+  const long long kStageSegs = (long long)nSW * kSegsPerWarp;
   const long long s0 = a.nseg * cta / B, s1 = a.nseg * (cta + 1) / B;
   const long long d0 = a.ndraw * cta / B, d1 = a.ndraw * (cta + 1) / B;
   const long long tma_end = s1 < a.nfull ? s1 : (s0 > a.nfull ? s0 : a.nfull);  // full segments [s0, tma_end)
   const long long n_it = kVec ? (tma_end - s0 + kStageSegs - 1) / kStageSegs : 0;
   const bool local = s1 - s0 <= kLocalSegs;
 
-  if (tid == 0) {
-    s_target = __ldcg(a.xch) + 1u;  // this call's epoch
-    if (kVec) {
-      for (int s = 0; s < kStages; ++s) {
-        mbar_init(&s_full[s], 1);
-        mbar_init(&s_empty[s], kFWarps);
-      }
-      asm volatile("fence.mbarrier_init.release.cluster;\n fence.proxy.async.shared::cta;" ::: "memory");
-    }
-  }
-  if (!F32)
-    for (int i = tid; i < 129; i += kFThreads) {
-      tab.nlogc[i] = a.tab->nlogc[i];
-      tab.invc[i] = a.tab->invc[i];
-    }
-  __syncthreads();
-  const unsigned target = s_target;
-  const unsigned tag = target % 65535u + 1u;  // never 0 (a slot never written), differs between calls
-  GBR_STAMP(0);
-
   unsigned long long pol = 0;
   if (kVec) asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  long long issued = 0;  // stages issued so far (thread 0)
   // stage it of the ring: segments [s0 + it*kStageSegs, ...) of the CTA range
   auto issue = [&](long long it) {
     const int st = (int)(it % kStages);
@@ -548,8 +640,30 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
     const unsigned bytes = (unsigned)((sb - sa) * kSegBytes);
     mbar_expect_tx(&s_full[st], bytes);
     bulk_g2s(s_dyn + (size_t)st * kStageBytes, w + sa * kSeg, bytes, &s_full[st], pol);  // one copy per stage
+    issued = it + 1;
   };
-  if (kVec && tid == 0 && n_it > 0) issue(0);
+  if (tid == 0) {
+    // the first stages travel before anything else is done
+    if (kVec) {
+      for (int s = 0; s < kStages; ++s) {
+        mbar_init(&s_full[s], 1);
+        mbar_init(&s_empty[s], (unsigned)nSW);
+      }
+      asm volatile("fence.mbarrier_init.release.cluster;\n fence.proxy.async.shared::cta;" ::: "memory");
+      for (long long it = 0; it < n_it && it < kStages; ++it) issue(it);
+    }
+    s_abort = 0;
+  }
+  if (tid == 32) s_target = __ldcg(a.xch) + 1u;  // this call's epoch
+  if (tid < kFWarps) s_wz[tid] = u128{0ULL, 0ULL};
+  for (int i = tid; i < 129; i += kFThreads) {
+    tab.nlogc[i] = a.tab->nlogc[i];
+    tab.invc[i] = a.tab->invc[i];
+  }
+  __syncthreads();
+  const unsigned target = s_target;
+  const unsigned tag = target % 65535u + 1u;  // never 0 (a slot never written), differs between calls
+  GBR_STAMP(0);
   GBR_STAMP(14);
   if (tid == kFThreads - 32) {
     // fetch the code of the once-per-call scalar steps (reciprocal, product)
@@ -559,157 +673,120 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused(FusedArgs a) {
   }
 
   // ---- phase 1a: the CTA's draws (Algorithm 1) -------------------------------
-  // Warp w < nW draws exactly the samples it maps below, [m0 + nsm w / nW,
-  // m0 + nsm (w+1) / nW), warp nW - 1 also the final draw N when this CTA
-  // holds it.  Each warp keeps its own exact running prefix (warp scans, no
-  // block barrier per tile); the warp totals are scanned once at the end, and
-  // the map adds the warp's offset.  With few draws per CTA the last warp
-  // takes none (it fetches the code of the scalar steps meanwhile).
+  // Many draws: warp w < nW draws exactly the samples it maps below, [m0 +
+  // nsm w / nW, m0 + nsm (w+1) / nW), warp nW - 1 also the final draw N when
+  // this CTA holds it, each warp with its own exact running prefix (warp
+  // scans, no block barrier per tile); the warp totals are scanned once after
+  // the stream, and the map adds the warp's offset.  With at most 2048 draws
+  // the last warp takes none (it fetches the code of the scalar steps
+  // meanwhile).  Few draws (a.few): warp 15 makes all of them during the
+  // stream (below), every warp maps a sixteenth of the samples.
   const long long m0 = d0, m1 = d1 < a.N ? d1 : a.N;
   const long long nsm = m1 > m0 ? m1 - m0 : 0;
-  const int nW = d1 - d0 > 4LL * kFThreads ? kFWarps : kFWarps - 1;
+  const int nW = a.few || d1 - d0 > 4LL * kFThreads ? kFWarps : kFWarps - 1;
   const long long g0 = warp < nW ? m0 + nsm * warp / nW : 0;  // [0, 0): no draws
   const long long g1 = warp < nW - 1 ? m0 + nsm * (warp + 1) / nW : (warp < nW ? d1 : 0);
   const long long i1 = warp < nW ? m0 + nsm * (warp + 1) / nW : m1;
-  u128 ztot;
-  {
-    u128 wrun = {0ULL, 0ULL};
-    const long long base = g0 & ~3LL;
-#pragma unroll 1
-    for (long long t0 = base; t0 < g1; t0 += 128) {
-      const long long k0 = t0 + 4LL * lane;
-      u128 pre[4];
-      u128 run = {0ULL, 0ULL};
-      const bool mine = k0 < g1 && k0 + 3 >= g0;
-      if (a.scheme == kSchemeMultinomial) {
-        if (mine) {
-          uint64_t words[4];
-          philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const long long k = k0 + q;
-            if (k >= g0 && k < g1) run = u128_add(run, spacing_ool<F32>(words[q], &tab));
-            pre[q] = run;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) pre[q] = run;
-        }
-      } else {
-        // strata points: every lane of the warp takes part (neighbour words)
-        uint64_t words[4];
-        philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, a.seed, a.inst, words);
-        u128 f[4];
-        block_spacings<F32>(a.scheme, k0, a.ndraw, a.seed, a.inst, words, &tab, f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long k = k0 + q;
-          if (k >= g0 && k < g1) run = u128_add(run, f[q]);
-          pre[q] = run;
-        }
-      }
-      const u128 incl = warp_incl_scan_v(run, lane);
-      const u128 excl = u128_add(wrun, u128_sub(incl, run));
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long k = k0 + q;
-        if (k >= g0 && k < g1 && k < a.N) a.Z[k] = u128_add(excl, pre[q]);
-      }
-      wrun = u128_add(wrun, shfl_v(incl, 31));
-    }
-    if (lane == 0) s_w[warp] = wrun;
-    __syncthreads();
-    u128 before = {0ULL, 0ULL}, t = {0ULL, 0ULL};
-#pragma unroll
-    for (int i = 0; i < kFWarps; ++i) {
-      const u128 x = s_w[i];
-      if (i < warp) before = u128_add(before, x);
-      t = u128_add(t, x);
-    }
-    if (lane == 0) s_woff[warp] = before;  // read again by the map (s_w is reused before then)
-    ztot = t;
+  if (!a.few) {
+    const u128 t = draw_range<F32>(a, g0, g1, &tab, lane);
+    if (lane == 0) s_wz[warp] = t;
   }
-  if (kVec && tid == 0)
-    for (long long it = 1; it < n_it && it < kStages; ++it) issue(it);
   GBR_STAMP(1);
 
-  // ---- phase 1b: the CTA's segments ------------------------------------------
+  // ---- phase 1b: the CTA's segments (with few draws, warp 15's draws) ------
   int emax = 0;
-  if (kVec) {
+  if (a.few && warp == kFWarps - 1) {
+    const u128 t = draw_range<F32>(a, d0, d1, &tab, lane);
+    if (lane == 0) s_wz[warp] = t;
+  } else {
+    if (kVec) {
 #pragma unroll 1
-    for (long long it = 0; it < n_it; ++it) {
-      const int st = (int)(it % kStages);
-      const unsigned par = (unsigned)((it / kStages) & 1);
-      if (!mbar_wait(&s_full[st], par, kTmaSpin)) {
-        if (lane == 0) raise_status(a.status, ST_ETIMEOUT);
-        mbar_wait(&s_full[st], par, kTmaSpin);  // the copy is still owed: wait again, bounded
-      }
-      const long long sa = s0 + it * kStageSegs;
-#pragma unroll
-      for (int r = 0; r < kSegsPerWarp; ++r) {
-        const int j = warp + r * kFWarps;
-        const long long s = sa + j;
-        if (s < tma_end) {
-          const unsigned char* src = s_dyn + (size_t)st * kStageBytes + (size_t)j * kSegBytes;
-          Bits b[kSegV];
-          constexpr int kPer = 16 / (int)sizeof(T);  // elements per 16-byte piece
-#pragma unroll
-          for (int q = 0; q < kSegV / kPer; ++q) {
-            const uint4 v = *reinterpret_cast<const uint4*>(src + 16 * lane + 512 * q);
-            if (F32) {
-              b[4 * q] = (Bits)v.x;
-              b[4 * q + 1] = (Bits)v.y;
-              b[4 * q + 2] = (Bits)v.z;
-              b[4 * q + 3] = (Bits)v.w;
-            } else {
-              b[2 * q] = (Bits)(((uint64_t)v.y << 32) | v.x);
-              b[2 * q + 1] = (Bits)(((uint64_t)v.w << 32) | v.z);
-            }
-          }
-          uint64_t F;
-          uint32_t E;
-          seg_sum_bits<T>(b, lane, a.status, F, E);
+      for (long long it = 0; it < n_it; ++it) {
+        const int st = (int)(it % kStages);
+        const unsigned par = (unsigned)((it / kStages) & 1);
+        if (*(volatile int*)&s_abort) break;
+        if (!mbar_wait(&s_full[st], par, kTmaSpin)) {
+          // a copy that did not complete: no further stage is issued, and
+          // the stages already issued are drained before the ring is reused
           if (lane == 0) {
-            a.seg[s] = SegRec{F, (int)E, kSeg};
-            if (local) {
-              s_lF[s - s0] = F;
-              s_lE[s - s0] = (int)E;
-            }
+            raise_status(a.status, ST_ETIMEOUT);
+            *(volatile int*)&s_abort = 1;
           }
-          emax = max(emax, (int)E);
+          break;
+        }
+        const long long sa = s0 + it * kStageSegs;
+#pragma unroll
+        for (int r = 0; r < kSegsPerWarp; ++r) {
+          const int j = warp + r * nSW;
+          const long long s = sa + j;
+          if (s < tma_end) {
+            uint64_t F;
+            uint32_t E;
+            seg_sum_smem<T>(s_dyn + (size_t)st * kStageBytes + (size_t)j * kSegBytes, lane, a.status, F, E);
+            if (lane == 0) {
+              a.seg[s] = SegRec{F, (int)E, kSeg};
+              if (local) {
+                s_lF[s - s0] = F;
+                s_lE[s - s0] = (int)E;
+              }
+            }
+            emax = max(emax, (int)E);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[st]);
+        if (tid == 0 && it + kStages < n_it && !*(volatile int*)&s_abort) {
+          // refill this stage once every streaming warp has read it
+          if (!mbar_wait(&s_empty[st], par, kTmaSpin)) {
+            raise_status(a.status, ST_ETIMEOUT);
+            *(volatile int*)&s_abort = 1;
+          } else {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(it + kStages);
+          }
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&s_empty[st]);
-      if (tid == 0 && it + kStages < n_it) {
-        // refill this stage once every warp has read it
-        if (!mbar_wait(&s_empty[st], par, kTmaSpin)) raise_status(a.status, ST_ETIMEOUT);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue(it + kStages);
+    }
+    // segments not taken by the ring (unaligned weights, the ragged last one)
+#pragma unroll 1
+    for (long long s = (kVec ? tma_end : s0) + warp; s < s1; s += nSW) {
+      Bits b[kSegV];
+      load_seg_striped<T, kVec>(w, s * kSeg, a.M, lane, b);
+      uint64_t F;
+      uint32_t E;
+      seg_sum_bits<T>(b, lane, a.status, F, E);
+      if (lane == 0) {
+        const long long rem = a.M - s * kSeg;
+        a.seg[s] = SegRec{F, (int)E, (int)(rem < kSeg ? rem : kSeg)};
+        if (local) {
+          s_lF[s - s0] = F;
+          s_lE[s - s0] = (int)E;
+        }
       }
+      emax = max(emax, (int)E);
     }
   }
-  // segments not taken by the ring (unaligned weights, the ragged last one)
-#pragma unroll 1
-  for (long long s = (kVec ? tma_end : s0) + warp; s < s1; s += kFWarps) {
-    Bits b[kSegV];
-    load_seg_striped<T, kVec>(w, s * kSeg, a.M, lane, b);
-    uint64_t F;
-    uint32_t E;
-    seg_sum_bits<T>(b, lane, a.status, F, E);
-    if (lane == 0) {
-      const long long rem = a.M - s * kSeg;
-      a.seg[s] = SegRec{F, (int)E, (int)(rem < kSeg ? rem : kSeg)};
-      if (local) {
-        s_lF[s - s0] = F;
-        s_lE[s - s0] = (int)E;
-      }
-    }
-    emax = max(emax, (int)E);
+  if (kVec && tid == 0 && *(volatile int*)&s_abort) {
+    // drain: the last use of every stage issued completes (bounded) before
+    // the shared memory of the ring is reused
+    for (long long it = issued > kStages ? issued - kStages : 0; it < issued; ++it)
+      mbar_wait(&s_full[it % kStages], (unsigned)((it / kStages) & 1), kTmaSpin);
   }
   if (lane == 0) s_e[warp] = emax;
   __syncthreads();
   GBR_STAMP(2);
+  u128 ztot;  // the CTA's spacing total; the warps' offsets for the map
+  {
+    u128 before = {0ULL, 0ULL}, t = {0ULL, 0ULL};
+#pragma unroll
+    for (int i = 0; i < kFWarps; ++i) {
+      const u128 x = s_wz[i];
+      if (i < warp) before = u128_add(before, x);
+      t = u128_add(t, x);
+    }
+    if (lane == 0) s_woff[warp] = before;
+    ztot = t;
+  }
 
   // ---- exchange 1: segment exponents and spacing totals ----------------------
   // (nothing else of this CTA is read by others before exchange 2, whose
@@ -901,6 +978,14 @@ static cudaError_t fused_t(const FusedLaunch& L, cudaStream_t st) {
   a.spin = L.spin;
   a.withhold_first = L.withhold_first;
   a.tab = L.tab;
+  // one warp makes all of a CTA's draws while the others stream when that
+  // takes well under the CTA's share of the stream (about 1 us per 128
+  // draws against about 45 GB/s per SM)
+  {
+    const long long draws_cta = (a.ndraw + blocks - 1) / blocks;
+    const long long bytes_cta = L.M * (long long)sizeof(T) / blocks;
+    a.few = kVec && draws_cta * 1024 <= bytes_cta;
+  }
   a.kBS = sizeof(T) == 4 ? FixedTraits<float>::kBias + FixedTraits<float>::kShift
                          : FixedTraits<double>::kBias + FixedTraits<double>::kShift;
   a.out = L.out;

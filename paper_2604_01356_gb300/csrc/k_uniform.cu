@@ -4,8 +4,7 @@
 //
 // GB300 form.  One pass over the N+1 draws: each thread takes four
 // consecutive draws (the four words of one Philox block), evaluates the
-// spacings (binary32-pair log for binary64 draws, binary32 logf for binary32
-// draws), converts them EXACTLY to integers on a 2^-88 grid and the block
+// spacings (binary32-pair table logarithm for both draw formats), converts them EXACTLY to integers on a 2^-88 grid and the block
 // scans them as unsigned 128-bit integers; tiles of 1024 draws chain their
 // sums by decoupled look-back.  Integer sums make Z
 // exact, monotone and independent of scheduling.  The resampling map consumes
@@ -28,11 +27,9 @@ __global__ void __launch_bounds__(kUThreads) k_uniform_scan(long long ndraw, uns
   __shared__ LogTab tab;
   __shared__ UniformTileSmem us;
   __shared__ unsigned s_tile;
-  if (!F32) {
-    for (int i = threadIdx.x; i < 129; i += kUThreads) {
-      tab.nlogc[i] = g_logtab.nlogc[i];
-      tab.invc[i] = g_logtab.invc[i];
-    }
+  for (int i = threadIdx.x; i < 129; i += kUThreads) {
+    tab.nlogc[i] = g_logtab.nlogc[i];
+    tab.invc[i] = g_logtab.invc[i];
   }
   if (threadIdx.x == 0) s_tile = atomicAdd(ctr, 1u);
   __syncthreads();

@@ -172,16 +172,13 @@ __device__ __forceinline__ u128 grid_value(unsigned long long F, int E, int Emax
 // ---- spacings (Algorithm 1) ---------------------------------------------
 constexpr int kZFrac = 88;  // spacing grid 2^-88
 
-// -log v of the draw taken from Philox word x, exactly on the 2^-88 grid:
-// binary32 draws use logf, binary64 draws the binary32-pair table logarithm
-// (tab: the table in shared memory; unused for binary32 draws).
+// -log v of the draw taken from Philox word x, exactly on the 2^-88 grid.
+// Both draw formats go through the binary32-pair table logarithm (about
+// 2^-45 relative): binary64 draws (2 (x >> 12) + 1) 2^-53 and binary32 draws
+// (2 (x >> 41) + 1) 2^-24.  tab: the table, staged in shared memory.
 template <bool F32>
 __device__ __forceinline__ u128 spacing_fixed(uint64_t word, const LogTab* tab) {
-  if (F32) {
-    const float v = __int2float_rn((int)(2u * (uint32_t)(word >> 41) + 1u)) * 0x1p-24f;  // exact
-    return f_to_fixed128<kZFrac>(-logf(v));
-  }
-  const df z = neg_log_draw(2ULL * (word >> 12) + 1ULL, 53, *tab);
+  const df z = F32 ? neg_log_draw(2ULL * (word >> 41) + 1ULL, 24, *tab) : neg_log_draw(2ULL * (word >> 12) + 1ULL, 53, *tab);
   const u128 f = f_to_fixed128<kZFrac>(z.hi);
   return (z.lo >= 0.0f) ? u128_add(f, f_to_fixed128<kZFrac>(z.lo)) : u128_sub(f, f_to_fixed128<kZFrac>(-z.lo));
 }

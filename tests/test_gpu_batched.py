@@ -103,11 +103,12 @@ def test_batched_against_oracle(g, h):
     g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), K, 4, out, woff, roff)
     assert h.status() == g.RS_OK
     got = host(out)
+    assert np.count_nonzero(got != r_ref) <= 2
     for k in range(K):
         a, b = int(roff[k]), int(roff[k + 1])
         Wk, _ = oracle.cumulative(w[woff[k]:woff[k + 1]])
         Uk = oracle.sorted_uniform(b - a, 4, k, single=True)
-        assert_boundary_only(got[a:b], r_ref[a:b], Wk, Uk, abs_tol=ABS_F32, max_frac=0.05)
+        assert_boundary_only(got[a:b], r_ref[a:b], Wk, Uk, abs_tol=ABS_F32, max_frac=0.0)
 
 
 def test_batched_large_k_identity_order(g, h):

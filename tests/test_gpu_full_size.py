@@ -120,15 +120,16 @@ def test_stress_f64_full(g, h, stress):
 
 def test_stress_f32_comp_full(g, h, stress):
     """The same instance in binary32 with compensated sums: indices within
-    4 * 2^-23 of a boundary of the oracle's binary32-weight W may differ, and
-    the cumulative weights stay within that bound of the binary64 ones."""
+    4 * 2^-23 of a boundary of the oracle's binary32-weight W may differ (the
+    stated bound), at most two do (what the path achieves), and the
+    cumulative weights stay within that bound of the binary64 ones."""
     wl = stress
     r_ref, W_ref, U_ref = oracle.resample(wl.w32, wl.N, wl.seed, single=True)
     wd = torch.from_numpy(wl.w32).cuda()
     out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
     g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out, None, g.opts(prec=g.RS_F32_COMP))
     assert h.status() == g.RS_OK
-    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.0)
     W32 = torch.empty(wl.M, dtype=torch.float64, device="cuda")
     g.rs_cumulative(h.h, wd, wl.M, W32, g.opts(prec=g.RS_F32_COMP))
     W64_ref, _ = oracle.cumulative(wl.w)
@@ -137,7 +138,8 @@ def test_stress_f32_comp_full(g, h, stress):
 
 def test_batched_full(g, h):
     """8,192 EnGMF-shaped binary32 instances in one persistent launch: every
-    index of every instance against the oracle's per-instance path."""
+    index of every instance against the oracle's per-instance path; at most
+    two differ, each on a boundary of its own instance."""
     wl = workloads.make("batched")
     K = wl.info["K"]
     r_ref = oracle.resample_batched(wl.w, wl.woff, wl.roff, wl.seed, single=True)
@@ -147,13 +149,16 @@ def test_batched_full(g, h):
     assert h.status() == g.RS_OK
     r = host(out)
     mism = np.nonzero(r != r_ref)[0]
-    # a mismatch must sit on a boundary of its own instance's binary32-weight W
-    assert mism.size <= 1e-4 * r.size, mism.size
-    for i in mism[:200]:
-        k = int(np.searchsorted(wl.roff, i, side="right") - 1)
+    assert mism.size <= 2, mism.size
+    # every mismatch must sit on a boundary of its own instance's
+    # binary32-weight W (each instance with a mismatch is recomputed once)
+    inst = np.searchsorted(wl.roff, mism, side="right") - 1
+    for k in np.unique(inst):
+        k = int(k)
         a, b = int(wl.woff[k]), int(wl.woff[k + 1])
         rr, W, U = oracle.resample(wl.w[a:b], int(wl.roff[k + 1] - wl.roff[k]), wl.seed, instance=k, single=True)
-        j = i - int(wl.roff[k])
-        assert rr[j] == r_ref[i]
-        lo, hi = sorted((int(r[i]), int(rr[j])))
-        assert np.all(np.abs(U[j] - W[lo:hi]) <= ABS_F32)
+        for i in mism[inst == k]:
+            j = int(i) - int(wl.roff[k])
+            assert rr[j] == r_ref[i]
+            lo, hi = sorted((int(r[i]), int(rr[j])))
+            assert np.all(np.abs(U[j] - W[lo:hi]) <= ABS_F32), (k, j)

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import ABS_F32, REL_F64, assert_boundary_only
+from parity_util import ABS_F32, REL_F64, REL_U_F32, assert_boundary_only
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,7 +80,8 @@ def test_sorted_uniform_f32_comp(g, h, N):
     got = host(U)
     ref = oracle.sorted_uniform(N, 9, 1, single=True)
     assert np.all(np.diff(got) >= 0)
-    assert np.max(np.abs(got - ref)) <= ABS_F32
+    assert np.max(np.abs(got - ref)) <= ABS_F32  # the stated bound
+    assert np.max(np.abs(got - ref) / ref) <= REL_U_F32  # what the path achieves
 
 
 # ----------------------------------------------------- cumulative (Eq.3) --
@@ -209,7 +210,7 @@ def test_resample_w_unaligned_weights(g, h, prec):
     assert np.array_equal(ra, host(b))
     r_ref, W_ref, U_ref = oracle.resample(w, N, 5, instance=1, single=prec == "f32")
     if prec == "f32":
-        assert_boundary_only(ra, r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+        assert_boundary_only(ra, r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.0)
     else:
         assert_boundary_only(ra, r_ref, W_ref, U_ref, rel=REL_F64)
     z = torch.full((1,), -7, dtype=torch.int32, device="cuda")
@@ -238,7 +239,7 @@ def test_resample_w_f32_comp(g, h, M, N):
     out = torch.empty(N, dtype=torch.int32, device="cuda")
     g.rs_resample_w(h.h, dev(w), M, N, 31, 0, out, None, g.opts(prec=g.RS_F32_COMP))
     assert h.status() == g.RS_OK
-    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.02)
+    assert_boundary_only(host(out), r_ref, W_ref, U_ref, abs_tol=ABS_F32, max_frac=0.0)
 
 
 @pytest.mark.parametrize("algo", ["dac", "binary", "linear"])
@@ -263,12 +264,13 @@ def test_resample_batched_matches_instances(g, h):
     g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), K, 3, out, woff, roff)
     assert h.status() == g.RS_OK
     got = host(out)
+    assert np.count_nonzero(got != r_ref) <= 2
     for k in range(K):
         a, b = int(roff[k]), int(roff[k + 1])
         wk = w[woff[k]:woff[k + 1]]
         Wk, _ = oracle.cumulative(wk)
         Uk = oracle.sorted_uniform(b - a, 3, k, single=True)
-        assert_boundary_only(got[a:b], r_ref[a:b], Wk, Uk, abs_tol=ABS_F32, max_frac=0.05)
+        assert_boundary_only(got[a:b], r_ref[a:b], Wk, Uk, abs_tol=ABS_F32, max_frac=0.0)
 
 
 # ----------------------------------------------------- device errors ----
@@ -294,7 +296,7 @@ def test_zero_sum_latches_status(g, h):
 def test_bounded_wait_times_out_and_context_survives(g, h):
     """Fault injection on the host side: the first look-back tile of the
     spacing scan withholds its publication; every later tile's wait runs out
-    after spin_limit polls (tiles of 256 draws, so 40 tiles here)."""
+    after spin_limit polls (tiles of 1024 draws, so 10 tiles here)."""
     N = 10_000
     U = torch.empty(N, dtype=torch.float64, device="cuda")
     g.rs_sorted_uniform(h.h, N, 5, 7, U, g.opts(spin_limit=200, debug_flags=1))
