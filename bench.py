@@ -340,10 +340,13 @@ def run_ours(args):
             torch.cuda.empty_cache()
             line["bootstrap"] = single_measure(g, h, dev, stream, "bootstrap", hbm)
             line["stress"] = single_measure(g, h, dev, stream, "stress", hbm)
+            line["small"] = small_measure(g, h, dev, stream)
+            line["accuracy_vs_oracle"] = accuracy_report(g, h, dev, stream)
     else:
         line["e2e"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl.w, N, seed)
+        line["cpu_allcore"] = cpu_allcore()
     h.close()
     if dist:
         dist.destroy_process_group()
@@ -391,7 +394,8 @@ def e2e_measure(g, h, wl, dev, stream, K, inst):
 
 def map_only(g, h, wl, dev, stream, K=50):
     """The paper's timing protocol: sampling steps only (W given): sorted
-    uniforms + map, for the three maps, on the engmf instance."""
+    uniforms + map, for the three maps, on the engmf instance; the DaC map
+    with the leaf size its autotuner picks (kept in the handle)."""
     import torch
     M, N, seed = wl.M, wl.N, wl.seed
     wd = torch.from_numpy(wl.w).to(dev)
@@ -400,6 +404,9 @@ def map_only(g, h, wl, dev, stream, K=50):
     res = {}
     with torch.cuda.stream(stream):
         g.rs_cumulative(h.h, wd, M, W, stream=stream)
+        # the DaC leaf size picked by the library's autotuner for this M/N
+        best = g.rs_autotune_map(h.h, W, M, N, seed, out, stream=stream)
+        res["dac_tuned_leaf_L"] = best.leaf_L
         for name, algo in [("dac", g.RS_MAP_DAC), ("binary", g.RS_MAP_BINARY), ("linear", g.RS_MAP_LINEAR)]:
             o = g.opts(algo=algo)
             for _ in range(3):
@@ -510,9 +517,11 @@ def _time_calls(fn, stream, reps, warm=2):
 def batched_measure(g, h, dev, stream, hbm, reps=20):
     """8192 EnGMF-shaped instances (N_k ~ U{64..2048}, P_k ~ U{1..64},
     M_k = N_k P_k, binary32 weights): the persistent batched launch (autotuned,
-    replayed as a CUDA graph) against one binary64 rs_resample_w per instance
-    (plain launches, and the same loop captured in a graph), plus the binary32
-    cumulative-weight error against binary64 on a sample of instances."""
+    replayed as a CUDA graph) against the same persistent launch in binary64
+    (the weights widened) and, for context, one binary64 rs_resample_w per
+    instance (plain launches, and the same loop captured in a graph), plus
+    the binary32 cumulative-weight error against binary64 on a sample of
+    instances."""
     import torch
     wl = workloads.make("batched")
     w32, woff, roff, K = wl.w, wl.woff, wl.roff, wl.info["K"]
@@ -532,19 +541,36 @@ def batched_measure(g, h, dev, stream, hbm, reps=20):
     if h.status() != g.RS_OK:
         raise RuntimeError("device status after the batched run")
     del graph
-    # binary64 comparison: the same weights widened, one rs_resample_w per instance
+    # binary64 comparisons on the same weights widened: the same persistent
+    # launch in binary64 (the like-for-like comparator), and, for context, one
+    # rs_resample_w per instance (plain launches, and the same loop in a graph)
     w64 = wd.double()
     del wd
     o64 = g.opts(prec=g.RS_F64)
-    f64 = lambda s=None: g.rs_resample_batched(h.h, w64, wo, ro, K, wl.seed, out, woff, roff, o64,  # noqa: E731
-                                                stream=s or stream)
-    ms64 = _time_calls(f64, stream, 2, warm=1)
+    with torch.cuda.stream(stream):
+        g.rs_resample_batched(h.h, w64, wo, ro, K, wl.seed, out, woff, roff, o64, stream=stream)
+    torch.cuda.synchronize()
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp, stream=stream):
+        g.rs_resample_batched(h.h, w64, wo, ro, K, wl.seed, out, woff, roff, o64, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms64p = _time_calls(gp.replay, stream, reps)
+    del gp
+
+    # one rs_resample_w per instance inside the library (debug bit 2: every
+    # instance through the cooperative single-instance launch)
+    o64i = g.opts(prec=g.RS_F64, debug_flags=4)
+    per_instance = lambda s=None: g.rs_resample_batched(  # noqa: E731
+        h.h, w64, wo, ro, K, wl.seed, out, woff, roff, o64i, stream=s or stream)
+    ms64 = _time_calls(per_instance, stream, 2, warm=1)
     g64 = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g64, stream=stream):
-        f64(torch.cuda.current_stream())
+        per_instance(torch.cuda.current_stream())
     torch.cuda.synchronize()
     ms64g = _time_calls(g64.replay, stream, 3, warm=1)
     del g64
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the binary64 batched runs")
     # binary32-compensated W against binary64 W on 64 instances
     rng = np.random.default_rng(0)
     err = 0.0
@@ -563,6 +589,9 @@ def batched_measure(g, h, dev, stream, hbm, reps=20):
             "tuned": {"tile_threads": best.tile_threads, "leaf_L": best.leaf_L},
             "f32_batched_graph_us": ms32 * 1e3, "f32_particles_per_s": sumN / (ms32 * 1e-3),
             "f32_GBps": bytes32 / (ms32 * 1e-3) / 1e9, "f32_frac_of_hbm": bytes32 / (ms32 * 1e-3) / 1e9 / hbm,
+            "batched_f64_persistent_us": ms64p * 1e3, "f64_GBps": (8 * sumM + 4 * sumN) / (ms64p * 1e-3) / 1e9,
+            "f64_frac_of_hbm": (8 * sumM + 4 * sumN) / (ms64p * 1e-3) / 1e9 / hbm,
+            "speedup_f32_vs_f64_persistent": ms64p / ms32,
             "f64_per_instance_launches_us": ms64 * 1e3, "f64_per_instance_graph_us": ms64g * 1e3,
             "speedup_vs_f64_launches": ms64 / ms32, "speedup_vs_f64_graph": ms64g / ms32,
             "max_abs_W_err_f32comp_vs_f64": err, "W_err_bound": 4 * 2.0 ** -23, "err_sample": "64 instances"}
@@ -603,6 +632,167 @@ def single_measure(g, h, dev, stream, name, hbm, reps=20):
         res["index_mismatches_f32comp_vs_f64"] = int((outs["f32comp"] != outs["f64"]).sum().item())
     if h.status() != g.RS_OK:
         raise RuntimeError("device status after the %s run" % name)
+    return res
+
+
+def small_measure(g, h, dev, stream, reps=200):
+    """The small workload (M = 4,096 Exp(1) weights, N = 1,024): the whole
+    path per call (rs_resample_w, back-to-back calls on one stream) and the
+    sampling steps on a given W (sorted uniforms + each of the three maps,
+    rs_resample_W), as per-call microseconds; a launch-latency regime."""
+    import torch
+    import oracle
+    oracle.lib()
+    wl = workloads.make("small")
+    M, N, seed = wl.M, wl.N, wl.seed
+    wd = torch.from_numpy(wl.w).to(dev)
+    W = torch.from_numpy(oracle.cumulative(wl.w)[0]).to(dev)
+    out = torch.empty(N, dtype=torch.int32, device=dev)
+    res = {"M": M, "N": N, "bytes": 8 * M + 4 * N}
+    ms = _time_calls(lambda: g.rs_resample_w(h.h, wd, M, N, seed, 0, out, stream=stream), stream, reps)
+    res["whole_path_us_per_call"] = ms * 1e3
+    res["whole_path_particles_per_s"] = N / (ms * 1e-3)
+    for name, algo in [("dac", g.RS_MAP_DAC), ("binary", g.RS_MAP_BINARY), ("linear", g.RS_MAP_LINEAR)]:
+        o = g.opts(algo=algo)
+        ms = _time_calls(lambda: g.rs_resample_W(h.h, W, M, N, seed, 0, out, o, stream=stream), stream, reps)
+        res["map_only_us_per_call_" + name] = ms * 1e3
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the small workload")
+    return res
+
+
+def accuracy_report(g, h, dev, stream):
+    """Every workload against the binary64 oracle: max |W - W_oracle| of the
+    cumulative weights, max |U - U_oracle| (absolute and relative) of the
+    sorted uniforms, and the index mismatches of the whole path with how many
+    of them lie on a boundary within the stated tolerance (1e-12 relative for
+    binary64; 4 * 2^-23 absolute for compensated binary32).  Binary32 rows use
+    the oracle evaluated on the same binary32 weights and draws; the stress
+    row also gives W32 against the oracle's binary64 W of the unrounded
+    weights.  The batched row covers a sample of 64 instances."""
+    import torch
+    import oracle
+    oracle.lib()
+
+    def one(w_np, N, seed, inst, prec):
+        f32 = prec == "f32comp"
+        M = w_np.shape[0]
+        o = g.opts(prec=g.RS_F32_COMP if f32 else g.RS_F64)
+        wd = torch.from_numpy(w_np).to(dev)
+        Wg = torch.empty(M, dtype=torch.float64, device=dev)
+        Ug = torch.empty(N, dtype=torch.float64, device=dev)
+        r = torch.empty(N, dtype=torch.int32, device=dev)
+        with torch.cuda.stream(stream):
+            g.rs_cumulative(h.h, wd, M, Wg, o, stream=stream)
+            g.rs_sorted_uniform(h.h, N, seed, inst, Ug, o, stream=stream)
+            g.rs_resample_w(h.h, wd, M, N, seed, inst, r, None, o, stream=stream)
+        torch.cuda.synchronize()
+        if h.status() != g.RS_OK:
+            raise RuntimeError("device status in the accuracy report")
+        r_ref, W_ref, U_ref = oracle.resample(w_np, N, seed, instance=inst, single=f32)
+        Wh, Uh, rh = Wg.cpu().numpy(), Ug.cpu().numpy(), r.cpu().numpy()
+        mism = np.nonzero(rh != r_ref)[0]
+        on_b = 0
+        for i in mism:
+            a, b = sorted((int(rh[i]), int(r_ref[i])))
+            Wk = W_ref[a:b]
+            tol = 4 * 2.0 ** -23 if f32 else 1e-12 * Wk
+            on_b += int(np.all(np.abs(U_ref[i] - Wk) <= tol))
+        return {"max_abs_W_err": float(np.max(np.abs(Wh - W_ref))),
+                "max_rel_W_err": float(np.max(np.abs(Wh - W_ref) / np.maximum(W_ref, 1e-300))),
+                "max_abs_U_err": float(np.max(np.abs(Uh - U_ref))),
+                "max_rel_U_err": float(np.max(np.abs(Uh - U_ref) / U_ref)),
+                "index_mismatches": int(mism.size), "mismatches_on_boundary": on_b, "N": int(N), "M": int(M)}
+
+    rep = {}
+    for name in ("small", "engmf", "bootstrap", "stress"):
+        wl = workloads.make(name)
+        rep[name + ".f64"] = one(wl.w, wl.N, wl.seed, 0, "f64")
+        if wl.w32 is not None:
+            row = one(wl.w32, wl.N, wl.seed, 0, "f32comp")
+            Wg = torch.empty(wl.M, dtype=torch.float64, device=dev)
+            g.rs_cumulative(h.h, torch.from_numpy(wl.w32).to(dev), wl.M, Wg, g.opts(prec=g.RS_F32_COMP),
+                            stream=stream)
+            torch.cuda.synchronize()
+            W64, _ = oracle.cumulative(wl.w)
+            row["max_abs_W_err_vs_f64_weights"] = float(np.max(np.abs(Wg.cpu().numpy() - W64)))
+            rep[name + ".f32comp"] = row
+        del wl
+        torch.cuda.empty_cache()
+    wl = workloads.make("batched")
+    rng = np.random.default_rng(0)
+    agg = {}
+    for k in sorted(rng.choice(wl.info["K"], size=64, replace=False)):
+        a, b = int(wl.woff[k]), int(wl.woff[k + 1])
+        Nk = int(wl.roff[k + 1] - wl.roff[k])
+        for prec, wk in (("f32comp", wl.w[a:b]), ("f64", wl.w[a:b].astype(np.float64))):
+            row = one(wk, Nk, wl.seed, int(k), prec)
+            t = agg.setdefault("batched." + prec, {"sample": "64 instances", "index_mismatches": 0,
+                                                    "mismatches_on_boundary": 0, "N": 0, "max_abs_W_err": 0.0,
+                                                    "max_abs_U_err": 0.0, "max_rel_U_err": 0.0})
+            for key in ("index_mismatches", "mismatches_on_boundary", "N"):
+                t[key] += row[key]
+            for key in ("max_abs_W_err", "max_abs_U_err", "max_rel_U_err"):
+                t[key] = max(t[key], row[key])
+    rep.update(agg)
+    return rep
+
+
+def _allcore_worker(job):
+    """One process of the all-core CPU leg: the oracle as it stands on whole
+    instances (engmf instances, or a slice of the batched instances)."""
+    kind, lo, hi = job
+    import oracle
+    oracle.lib()
+    t0 = time.perf_counter()
+    n = 0
+    if kind == "engmf":
+        wl = workloads.make("engmf")
+        t0 = time.perf_counter()
+        for inst in range(lo, hi):
+            oracle.resample(wl.w, wl.N, wl.seed, instance=inst)
+            n += wl.N
+    else:
+        w, woff, roff = workloads.weights_batched(K=workloads.CONFIGS["batched"]["K"],
+                                                  seed=workloads.CONFIGS["batched"]["seed"])
+        t0 = time.perf_counter()
+        for k in range(lo, hi):
+            a, b = int(woff[k]), int(woff[k + 1])
+            Nk = int(roff[k + 1] - roff[k])
+            oracle.resample(w[a:b], Nk, workloads.PHILOX_SEED["batched"], instance=k, single=True)
+            n += Nk
+    return n, time.perf_counter() - t0
+
+
+def cpu_allcore():
+    """The oracle as it stands, one process per host core (spawned), on
+    independent instances: engmf instances (instance ids 0..P-1, two each) and
+    a slice of the batched workload's instances; particles/s over the slowest
+    process, with the core count and CPU model."""
+    import multiprocessing as mp
+    import platform
+    P = os.cpu_count() or 1
+    model = platform.processor() or platform.machine()
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    res = {"cores": P, "cpu_model": model, "kind": "oracle", "unit": UNIT}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(P) as pool:
+        out = pool.map(_allcore_worker, [("engmf", 2 * p, 2 * p + 2) for p in range(P)])
+        n = sum(o[0] for o in out)
+        res["engmf"] = {"value": n / max(o[1] for o in out),
+                        "sample": "%d full engmf instances (2 per process) end to end" % (2 * P)}
+        per = 16
+        out = pool.map(_allcore_worker, [("batched", per * p, per * p + per) for p in range(P)])
+        n = sum(o[0] for o in out)
+        res["batched"] = {"value": n / max(o[1] for o in out),
+                          "sample": "the first %d batched instances (%d per process, binary32 weights and draws)"
+                                    % (per * P, per)}
     return res
 
 

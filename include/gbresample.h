@@ -103,7 +103,13 @@ typedef struct {
                           wait runs out and RS_ETIMEOUT is latched (results are then
                           unspecified).  Nothing faults.  Bit 1: rs_resample_w uses
                           the multi-kernel path instead of the single cooperative
-                          launch (identical results; for comparison). */
+                          launch (identical results; for comparison).  Bit 2: the
+                          one-CTA paths of small instances (rs_resample_w up to
+                          32,768 weights and 2,048 samples; the sorted uniforms of
+                          rs_sorted_uniform and rs_resample_W up to 2,047
+                          samples) are not taken (identical results; for
+                          comparison).  Bit 0 also keeps the uniforms on the
+                          look-back scan whose wait it exercises. */
   int32_t tile_threads; /* rs_resample_batched: threads per CTA, 128, 256 or 512
                            (0 = the autotuned or default value); ignored elsewhere */
   int32_t scheme;      /* rs_scheme of the N uniforms (default RS_SCHEME_MULTINOMIAL) */
@@ -122,8 +128,13 @@ rs_status rs_destroy(rs_handle* h);
  *  out_idx [N] int32 sample indices, written.
  *  W_out   [M] binary64 cumulative weights W (Eq. 3), written if not NULL.
  *  seed, instance select the Philox stream of the N+1 draws.
- * The map is always the segmented divide and conquer described in the
- * library's design notes; opts->algo is ignored here. */
+ * Launch forms, all giving identical indices: an instance of at most 32,768
+ * weights and 2,048 samples runs on one CTA (one launch); otherwise one
+ * cooperative launch of one CTA per SM (a multi-kernel sequence when the
+ * device cannot hold that grid, or when W_out is requested).  The map is the
+ * segmented divide and conquer (exact segment sums and their prefixes, the
+ * segment of each key, the element from that segment's exact prefixes);
+ * opts->algo is ignored here. */
 rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
                         int32_t* out_idx, double* W_out, const rs_opts* opts, void* stream);
 
@@ -245,12 +256,15 @@ rs_status rs_gather(rs_handle* h, const void* x, int64_t M, int64_t row_bytes, c
  *         the stream (not allowed during stream capture); when given it reads
  *         nothing back from the device.
  *  out_idx [r_off[K]] int32 indices, local to each instance, written.
- * RS_F32_COMP: one persistent launch processes every instance of at most
- * 262,144 weights (one CTA per instance, taken from an atomic queue in order
- * of decreasing M_k); larger instances go through the single-instance path
- * first, on the same stream.  RS_F64: one rs_resample_w per instance.
- * opts->tile_threads and opts->leaf_L select the CTA size and the leaf
- * threshold; 0 takes the values rs_autotune_batched stored in the handle, or
+ * One persistent launch (either precision) processes every instance of at
+ * most 262,144 weights and 2,048 samples (one CTA per instance, taken from an
+ * atomic queue in order of decreasing M_k); larger instances go through the
+ * single-instance path first, on the same stream.  opts->debug_flags bit 2
+ * sends every instance through rs_resample_w's cooperative launch instead
+ * (identical indices; the per-instance comparison).  opts->tile_threads and
+ * opts->leaf_L select the CTA size and the leaf threshold; 0 takes the values
+ * rs_autotune_batched stored in the handle (or rs_tuning_load read) for the
+ * batch's precision and nearest M/N bucket, or
  * defaults (256, 4). */
 rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
                               const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
@@ -266,6 +280,40 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
 rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
                               const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
                               const rs_opts* opts, rs_opts* best, void* stream);
+
+/* Autotuner of the divide-and-conquer map given W (Alg. 5, Sec. III; the
+ * paper's concluding recommendation ties the best sampler to M/N, and Table
+ * I's cost N log2(M/N + 1) to the leaf size).  Draws the N sorted uniforms of
+ * the stream (seed, instance 0) into the handle's workspace, then times
+ * rs_map with RS_MAP_DAC for every leaf size 1, 2, 4, ..., 256 (one warm-up,
+ * three timed runs, CUDA events on `stream`), keeps the fastest in the handle
+ * under the key (RS_F64, M/N bucket round(log2(M/N))) for later calls with
+ * opts->leaf_L == 0, and writes it to *best (may be NULL): best->algo,
+ * best->leaf_L.
+ *  W        [M] binary64 cumulative weights (device, read only).
+ *  out_idx  [N] int32 device scratch (overwritten).
+ * Synchronises the stream; call it before any stream capture. */
+rs_status rs_autotune_map(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, int32_t* out_idx,
+                          rs_opts* best, void* stream);
+
+/* Persistence of tuned settings.  rs_tuning_save writes every setting the
+ * handle holds (from rs_autotune_map, rs_autotune_batched or an earlier
+ * load) to the JSON file at `path`, each keyed by (GPU name, kind "map_dac"
+ * or "batched", dtype "f64" or "f32", M/N bucket), keeping the file's entries
+ * of other GPUs.  rs_tuning_load adds the file's entries for this handle's
+ * GPU (entries of other GPUs are skipped); RS_EINVAL when the file cannot be
+ * read or is not a tuning file.  rs_create loads the file named by the
+ * environment variable GBRESAMPLE_TUNING, when set (a missing or malformed
+ * file leaves the defaults).  Host only; no device work. */
+rs_status rs_tuning_save(rs_handle* h, const char* path);
+rs_status rs_tuning_load(rs_handle* h, const char* path);
+
+/* The setting the handle would use for an instance (or batch) of M weights
+ * and N samples: kind 0 = the DaC map given W, 1 = the batched kernel;
+ * precision RS_F64 / RS_F32_COMP.  out->leaf_L and out->tile_threads are 0
+ * when nothing is tuned for that kind and precision (the nearest tuned M/N
+ * bucket is used otherwise). */
+rs_status rs_tuning_get(rs_handle* h, int32_t kind, int32_t precision, int64_t M, int64_t N, rs_opts* out);
 
 /* Synchronise `stream`, return the device status latched since the previous
  * call (RS_OK if none) and clear it. */

@@ -14,5 +14,6 @@ from ._binding import (  # noqa: F401
     rs_create, rs_destroy, rs_get_status, rs_last_error, rs_version,
     rs_resample_w, rs_resample_W, rs_sorted_uniform, rs_sorted_uniform_static, rs_cumulative, rs_map, rs_philox, rs_gather,
     rs_softmax_weights, rs_resample_logw,
-    rs_resample_batched, rs_autotune_batched, rs_trace_enable, rs_trace_collect, rs_trace_report, rs_trace_reset,
+    rs_resample_batched, rs_autotune_batched, rs_autotune_map, rs_tuning_save, rs_tuning_load, rs_tuning_get,
+    rs_trace_enable, rs_trace_collect, rs_trace_report, rs_trace_reset,
 )

@@ -66,6 +66,10 @@ def lib():
             "rs_resample_logw": (_ST, [_P, _P, _I64, _I64, _U64, _U64, _P, _OPTS, _P]),
             "rs_resample_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _P]),
             "rs_autotune_batched": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _U64, _P, _OPTS, _OPTS, _P]),
+            "rs_autotune_map": (_ST, [_P, _P, _I64, _I64, _U64, _P, _OPTS, _P]),
+            "rs_tuning_save": (_ST, [_P, ctypes.c_char_p]),
+            "rs_tuning_load": (_ST, [_P, ctypes.c_char_p]),
+            "rs_tuning_get": (_ST, [_P, _I32, _I32, _I64, _I64, _OPTS]),
             "rs_trace_enable": (_ST, [_P, ctypes.c_int]),
             "rs_trace_collect": (_ST, [_P, ctypes.c_int]),
             "rs_trace_report": (_ST, [_P, ctypes.c_char_p, _I64]),
@@ -197,6 +201,28 @@ def rs_autotune_batched(h, w, w_off, r_off, K, seed, out_idx, h_w_off=None, h_r_
                                         None if hr is None else hr.ctypes.data, seed, _ptr(out_idx), _opt(o),
                                         ctypes.byref(best), _stream(stream)))
     return best
+
+
+def rs_autotune_map(h, W, M, N, seed, out_idx, stream=None):
+    """Tunes the DaC map's leaf size on W; returns the chosen rs_opts."""
+    best = rs_opts()
+    _check(h, lib().rs_autotune_map(h, _ptr(W), M, N, seed, _ptr(out_idx), ctypes.byref(best), _stream(stream)))
+    return best
+
+
+def rs_tuning_save(h, path):
+    _check(h, lib().rs_tuning_save(h, str(path).encode()))
+
+
+def rs_tuning_load(h, path):
+    _check(h, lib().rs_tuning_load(h, str(path).encode()))
+
+
+def rs_tuning_get(h, kind, precision, M, N):
+    """kind 0: the DaC map given W, 1: the batched kernel; returns rs_opts."""
+    out = rs_opts()
+    _check(h, lib().rs_tuning_get(h, kind, precision, M, N, ctypes.byref(out)))
+    return out
 
 
 def rs_trace_enable(h, on=True):

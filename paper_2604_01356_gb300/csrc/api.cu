@@ -1,8 +1,10 @@
 // Host side of the C ABI declared in include/gbresample.h: argument checks,
 // the grow-only device workspace, launch sequencing and the device status
 // word.  Every entry point enqueues on the caller's stream and returns.
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,6 +22,15 @@ struct rs_trace_total {
   double ms;
 };
 
+// One tuned setting: the kind of call it applies to ("map_dac": the leaf size
+// of the divide-and-conquer map given W; "batched": CTA size and leaf
+// threshold of the persistent kernel), the weight precision, and the M/N
+// bucket round(log2(M/N)) of the instance (or of the whole batch).
+struct rs_tune_entry {
+  std::string gpu, kind, dtype;
+  int bucket = 0, threads = 0, leaf = 0;
+};
+
 struct rs_handle {
   int device = 0;
   int* status = nullptr;  // device status word (first device error wins)
@@ -31,7 +42,8 @@ struct rs_handle {
   cudaStream_t side = nullptr;    // second stream for work independent of the weights pass
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool tracing = false;
-  int tuned_threads = 0, tuned_leaf = 0;  // rs_autotune_batched's choice (0: none yet)
+  std::string gpu;                        // device name (the key of persisted tuning)
+  std::vector<rs_tune_entry> tuned;       // tuned settings (autotuners, rs_tuning_load)
   std::vector<rs_trace_pair> pending;
   std::vector<rs_trace_total> totals;
 };
@@ -60,6 +72,10 @@ using namespace gbr;
 constexpr long long kMaxLen = (1LL << 31) - 1;
 constexpr int kDefaultSpin = 1 << 22;
 constexpr int kStageCap = 512;  // shared-memory staging capacity of the DaC leaf (per warp)
+// Instances up to this many weights (and at most kBMaxN samples) run on one
+// CTA: the persistent kernel's single-instance form, one launch, no
+// inter-CTA exchange.
+constexpr long long kSmallM = 1LL << 15;
 
 rs_status fail(rs_handle* h, rs_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -138,7 +154,7 @@ rs_status read_opts(rs_handle* h, const rs_opts* o, Opts* out, int default_prec)
     if (o->tile_threads != 0 && o->tile_threads != 128 && o->tile_threads != 256 && o->tile_threads != 512)
       return fail(h, RS_EINVAL, "opts.tile_threads must be 0, 128, 256 or 512");
     r.threads = o->tile_threads;
-    if (o->debug_flags & ~3) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
+    if (o->debug_flags & ~7) return fail(h, RS_EINVAL, "opts.debug_flags: unknown bit");
     r.debug = o->debug_flags;
     r.algo = o->algo;
     r.prec = o->prec;
@@ -284,6 +300,99 @@ rs_status check_sizes(rs_handle* h, long long M, long long N) {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
+// ---- tuned settings ----------------------------------------------------------
+int mn_bucket(long long M, long long N) {
+  if (N <= 0 || M <= 0) return 0;
+  const double b = std::round(std::log2((double)M / (double)N));
+  return (int)(b < -16 ? -16 : (b > 40 ? 40 : b));
+}
+// The entry for (kind, dtype) with the nearest bucket (ties: the lower), or
+// nullptr.
+const rs_tune_entry* find_tune(const rs_handle* h, const char* kind, bool f32, int bucket) {
+  const rs_tune_entry* best = nullptr;
+  for (const auto& t : h->tuned) {
+    if (t.kind != kind || t.dtype != (f32 ? "f32" : "f64")) continue;
+    if (!best || std::abs(t.bucket - bucket) < std::abs(best->bucket - bucket) ||
+        (std::abs(t.bucket - bucket) == std::abs(best->bucket - bucket) && t.bucket < best->bucket))
+      best = &t;
+  }
+  return best;
+}
+void set_tune(rs_handle* h, const char* kind, bool f32, int bucket, int threads, int leaf) {
+  for (auto& t : h->tuned)
+    if (t.kind == kind && t.dtype == (f32 ? "f32" : "f64") && t.bucket == bucket) {
+      t.threads = threads;
+      t.leaf = leaf;
+      return;
+    }
+  rs_tune_entry t;
+  t.gpu = h->gpu;
+  t.kind = kind;
+  t.dtype = f32 ? "f32" : "f64";
+  t.bucket = bucket;
+  t.threads = threads;
+  t.leaf = leaf;
+  h->tuned.push_back(t);
+}
+// Reads the flat JSON written by rs_tuning_save: {"entries": [{"gpu": ...,
+// "kind": ..., "dtype": ..., "mn_bucket": n, "tile_threads": n, "leaf_L": n},
+// ...]}.  Entries of other GPUs are skipped.  Returns false when the text is
+// not of that form.
+bool parse_tuning(rs_handle* h, const std::string& text) {
+  const size_t e = text.find("\"entries\"");
+  if (e == std::string::npos) return false;
+  size_t i = text.find('[', e);
+  if (i == std::string::npos) return false;
+  std::vector<rs_tune_entry> got;
+  while (true) {
+    const size_t a = text.find('{', i), close = text.find(']', i);
+    if (a == std::string::npos || (close != std::string::npos && close < a)) break;
+    const size_t b = text.find('}', a);
+    if (b == std::string::npos) return false;
+    rs_tune_entry t;
+    bool ok_kind = false;
+    size_t p = a + 1;
+    while (p < b) {
+      const size_t k0 = text.find('"', p);
+      if (k0 == std::string::npos || k0 >= b) break;
+      const size_t k1 = text.find('"', k0 + 1);
+      const size_t colon = text.find(':', k1);
+      if (k1 == std::string::npos || colon == std::string::npos || colon >= b) return false;
+      const std::string key = text.substr(k0 + 1, k1 - k0 - 1);
+      size_t v = colon + 1;
+      while (v < b && (text[v] == ' ' || text[v] == '\n' || text[v] == '\t')) ++v;
+      std::string val;
+      if (v < b && text[v] == '"') {
+        const size_t v1 = text.find('"', v + 1);
+        if (v1 == std::string::npos || v1 > b) return false;
+        val = text.substr(v + 1, v1 - v - 1);
+        p = v1 + 1;
+      } else {
+        size_t v1 = v;
+        while (v1 < b && text[v1] != ',' && text[v1] != '}') ++v1;
+        val = text.substr(v, v1 - v);
+        p = v1;
+      }
+      if (key == "gpu") t.gpu = val;
+      else if (key == "kind") t.kind = val, ok_kind = true;
+      else if (key == "dtype") t.dtype = val;
+      else if (key == "mn_bucket") t.bucket = atoi(val.c_str());
+      else if (key == "tile_threads") t.threads = atoi(val.c_str());
+      else if (key == "leaf_L") t.leaf = atoi(val.c_str());
+    }
+    if (!ok_kind || (t.dtype != "f32" && t.dtype != "f64")) return false;
+    got.push_back(t);
+    i = b + 1;
+  }
+  for (const auto& t : got) {
+    if (t.gpu != h->gpu) continue;
+    if ((t.kind == "map_dac" && t.leaf >= 1 && t.leaf <= 1024 && !(t.leaf & (t.leaf - 1))) ||
+        (t.kind == "batched" && (t.threads == 128 || t.threads == 256 || t.threads == 512) && t.leaf >= 1))
+      set_tune(h, t.kind.c_str(), t.dtype == "f32", t.bucket, t.threads, t.leaf);
+  }
+  return true;
+}
+
 // Samples per warp group of the segmented map: about two warps' worth of
 // groups per SM slot, at least one sample each.
 int group_size(long long N) {
@@ -296,8 +405,9 @@ int group_size(long long N) {
 
 // DaC leaf size: the largest power of two L <= 256 whose expected W range
 // (L*M/N elements) fits the staging capacity; 1 when samples are sparse.
-int leaf_size(const Opts& o, long long M, long long N) {
+int leaf_size(const rs_handle* h, const Opts& o, long long M, long long N) {
   if (o.leaf_L > 0) return o.leaf_L;
+  if (const rs_tune_entry* t = find_tune(h, "map_dac", false, mn_bucket(M, N))) return t->leaf;
   double cap = (double)o.stage_max * (double)N / (double)M;
   int L = 1;
   while (L * 2 <= 256 && L * 2 <= cap) L *= 2;
@@ -372,7 +482,7 @@ rs_status enqueue_map(rs_handle* h, const Opts& o, const double* W, long long M,
     }
     default: {
       RS_TRACE(h, "map_dac", st);
-      RS_CK(h, launch_map_dac(W, M, U, N, leaf_size(o, M, N), o.stage_max, out, st));
+      RS_CK(h, launch_map_dac(W, M, U, N, leaf_size(h, o, M, N), o.stage_max, out, st));
       break;
     }
   }
@@ -405,6 +515,9 @@ rs_status rs_create(rs_handle** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaDeviceProp prop;
+  if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, h->device);
+  if (e == cudaSuccess) h->gpu = prop.name;
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (h->status) cudaFree(h->status);
@@ -416,7 +529,80 @@ rs_status rs_create(rs_handle** out) {
     delete h;
     return RS_ECUDA;
   }
+  // tuned settings persisted by an earlier rs_tuning_save (if any)
+  if (const char* path = getenv("GBRESAMPLE_TUNING")) {
+    if (*path) rs_tuning_load(h, path);  // a missing or malformed file leaves the defaults
+    h->err.clear();
+  }
   *out = h;
+  return RS_OK;
+}
+
+rs_status rs_tuning_save(rs_handle* h, const char* path) {
+  if (!h || !path) return RS_EINVAL;
+  // keep the file's entries of other GPUs
+  std::vector<rs_tune_entry> keep;
+  if (FILE* f = fopen(path, "rb")) {
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+    fclose(f);
+    rs_handle other;
+    for (size_t pos = 0; (pos = text.find("\"gpu\": \"", pos)) != std::string::npos;) {
+      const size_t a0 = pos + 8, b0 = text.find('"', a0);
+      if (b0 == std::string::npos) break;
+      other.gpu = text.substr(a0, b0 - a0);
+      pos = b0;
+      if (other.gpu == h->gpu) continue;
+      other.tuned.clear();
+      if (!parse_tuning(&other, text)) break;
+      for (const auto& t : other.tuned) {
+        bool dup = false;
+        for (const auto& k : keep)
+          dup |= k.gpu == t.gpu && k.kind == t.kind && k.dtype == t.dtype && k.bucket == t.bucket;
+        if (!dup) keep.push_back(t);
+      }
+    }
+  }
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(h, RS_EINVAL, std::string("cannot write ") + path);
+  fprintf(f, "{\n  \"format\": \"gbresample tuning 1\",\n  \"entries\": [");
+  bool first = true;
+  auto put = [&](const rs_tune_entry& t) {
+    fprintf(f, "%s\n    {\"gpu\": \"%s\", \"kind\": \"%s\", \"dtype\": \"%s\", \"mn_bucket\": %d, "
+               "\"tile_threads\": %d, \"leaf_L\": %d}",
+            first ? "" : ",", t.gpu.c_str(), t.kind.c_str(), t.dtype.c_str(), t.bucket, t.threads, t.leaf);
+    first = false;
+  };
+  for (const auto& t : keep) put(t);
+  for (const auto& t : h->tuned) put(t);
+  fprintf(f, "\n  ]\n}\n");
+  const bool ok = fclose(f) == 0;
+  return ok ? RS_OK : fail(h, RS_EINVAL, std::string("cannot write ") + path);
+}
+
+rs_status rs_tuning_load(rs_handle* h, const char* path) {
+  if (!h || !path) return RS_EINVAL;
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(h, RS_EINVAL, std::string("cannot read ") + path);
+  std::string text;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+  fclose(f);
+  if (!parse_tuning(h, text)) return fail(h, RS_EINVAL, std::string("not a tuning file: ") + path);
+  return RS_OK;
+}
+
+rs_status rs_tuning_get(rs_handle* h, int32_t kind, int32_t precision, int64_t M, int64_t N, rs_opts* out) {
+  if (!h || !out || (kind != 0 && kind != 1) || (precision != RS_F64 && precision != RS_F32_COMP)) return RS_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->prec = precision;
+  const rs_tune_entry* t = find_tune(h, kind == 0 ? "map_dac" : "batched", precision == RS_F32_COMP, mn_bucket(M, N));
+  if (!t) return RS_OK;
+  out->leaf_L = t->leaf;
+  out->tile_threads = t->threads;
   return RS_OK;
 }
 
@@ -532,6 +718,12 @@ rs_status rs_sorted_uniform(rs_handle* h, int64_t N, uint64_t seed, uint64_t ins
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(0, N, false, true, false);
   if ((s = ensure_ws(h, p.bytes))) return s;
+  if (N <= kUSmallMaxN && !(o.debug & 5)) {  // one CTA, one launch
+    RS_TRACE(h, "uniform_small", st);
+    RS_CK(h, launch_uniform_small(o.prec == RS_F32_COMP, N + 1, seed, instance, at<void>(h, p.o_Z), U_out, st,
+                                  o.scheme));
+    return RS_OK;
+  }
   if ((s = enqueue_clear(h, p, st))) return s;
   return enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, U_out, o, st);
 }
@@ -567,6 +759,13 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   if (W_out && !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be 8-byte aligned");
   if (N == 0 && !W_out) return RS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N > 0 && !W_out && !(o.debug & 6) && M <= kSmallM && N <= kBMaxN) {
+    // a small instance: the whole path on one CTA
+    RS_TRACE(h, "single_cta", st);
+    RS_CK(h, launch_batched(f32, w, nullptr, nullptr, nullptr, 1, seed, instance, M, N, 256, 4, out_idx, nullptr,
+                            h->status, st, o.scheme, static_cast<const LogTab*>(h->logtab)));
+    return RS_OK;
+  }
   const Plan p = make_plan(M, N, true, N > 0, false, W_out != nullptr);
   if (N > 0 && !W_out && !(o.debug & 2)) {
     // the whole path in one cooperative launch (when the device holds it);
@@ -639,8 +838,14 @@ rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uin
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Plan p = make_plan(0, N, false, true, true);
   if ((s = ensure_ws(h, p.bytes))) return s;
-  if ((s = enqueue_clear(h, p, st))) return s;
-  if ((s = enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, at<double>(h, p.o_U), o, st))) return s;
+  if (N <= kUSmallMaxN && !(o.debug & 5)) {  // the sorted uniforms by one CTA, one launch
+    RS_TRACE(h, "uniform_small", st);
+    RS_CK(h, launch_uniform_small(o.prec == RS_F32_COMP, N + 1, seed, instance, at<void>(h, p.o_Z),
+                                  at<double>(h, p.o_U), st, o.scheme));
+  } else {
+    if ((s = enqueue_clear(h, p, st))) return s;
+    if ((s = enqueue_uniforms(h, p, o.prec == RS_F32_COMP, seed, instance, at<double>(h, p.o_U), o, st))) return s;
+  }
   return enqueue_map(h, o, W, M, at<double>(h, p.o_U), N, out_idx, st);
 }
 
@@ -750,22 +955,25 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
   one.prec = o.prec;
   one.spin_limit = o.spin;
   one.scheme = o.scheme;
-  // instances the persistent kernel does not take: every one in binary64,
-  // the large ones in binary32
+  one.debug_flags = o.debug & 4;
+  const bool per_instance = (o.debug & 4) != 0;  // comparison: every instance on its own
+  // instances the persistent kernel does not take (more than kBMaxSeg
+  // segments or kBMaxN samples): one single-instance call each
   for (int32_t k = 0; k < K; ++k) {
     const long long Mk = wo[k + 1] - wo[k], Nk = ro[k + 1] - ro[k];
     if (Nk == 0) continue;
-    if (f32 && (Mk + kSegLen - 1) / kSegLen <= kBMaxSeg && Nk <= kBMaxN) continue;
+    if (!per_instance && (Mk + kSegLen - 1) / kSegLen <= kBMaxSeg && Nk <= kBMaxN) continue;
     const void* wk = static_cast<const char*>(w) + (size_t)wo[k] * esz;
     if ((s = rs_resample_w(h, wk, Mk, Nk, seed, (uint64_t)k, out_idx + ro[k], nullptr, &one, stream))) return s;
   }
-  if (!f32) return RS_OK;
+  if (per_instance) return RS_OK;
   Layout L;
   const size_t o_queue = L.take(256);
   const size_t o_order = L.take((size_t)K * sizeof(int));
   if ((s = ensure_ws(h, L.off))) return s;
-  const int threads = o.threads ? o.threads : (h->tuned_threads ? h->tuned_threads : 256);
-  const int leaf = o.leaf_L ? o.leaf_L : (h->tuned_leaf ? h->tuned_leaf : 4);
+  const rs_tune_entry* tb = find_tune(h, "batched", f32, mn_bucket(wo[K], ro[K]));
+  const int threads = o.threads ? o.threads : (tb ? tb->threads : 256);
+  const int leaf = o.leaf_L ? o.leaf_L : (tb ? tb->leaf : 4);
   {
     RS_TRACE(h, "batched_order", st);
     RS_CK(h, cudaMemsetAsync(at<unsigned>(h, o_queue), 0, 256, st));
@@ -773,10 +981,61 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
   }
   {
     RS_TRACE(h, "batched", st);
-    RS_CK(h, launch_batched_f32(static_cast<const float*>(w), reinterpret_cast<const long long*>(w_off),
-                                reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, threads, leaf,
-                                out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme,
-                                static_cast<const LogTab*>(h->logtab)));
+    RS_CK(h, launch_batched(f32, w, reinterpret_cast<const long long*>(w_off),
+                            reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, 0ULL, 0, 0,
+                            threads, leaf, out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme,
+                            static_cast<const LogTab*>(h->logtab)));
+  }
+  return RS_OK;
+}
+
+rs_status rs_autotune_map(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, int32_t* out_idx,
+                          rs_opts* best, void* stream) {
+  rs_status s = check_handle(h);
+  if (s) return s;
+  if ((s = check_sizes(h, M, N))) return s;
+  if (N == 0) return fail(h, RS_EINVAL, "N must be positive to tune the map");
+  if (!W || !aligned(W, 8)) return fail(h, RS_EINVAL, "W must be a non-NULL 8-byte aligned pointer");
+  if (!out_idx || !aligned(out_idx, 4)) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Opts o;
+  const Plan p = make_plan(0, N, false, true, true);
+  if ((s = ensure_ws(h, p.bytes))) return s;
+  if ((s = enqueue_clear(h, p, st))) return s;
+  if ((s = enqueue_uniforms(h, p, false, seed, 0, at<double>(h, p.o_U), o, st))) return s;
+  const double* U = at<double>(h, p.o_U);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RS_CK(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(h, cudaGetLastError(), "cudaEventCreate");
+  }
+  float best_ms = -1.0f;
+  int bl = 1;
+  o.algo = RS_MAP_DAC;
+  for (int L = 1; L <= 256 && !s; L *= 2) {
+    o.leaf_L = L;
+    if ((s = enqueue_map(h, o, W, M, U, N, out_idx, st))) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && !s; ++r) s = enqueue_map(h, o, W, M, U, N, out_idx, st);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess && !s) s = cuda_fail(h, e, "autotune timing");
+    if (!s && (best_ms < 0.0f || ms < best_ms)) {
+      best_ms = ms;
+      bl = L;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  set_tune(h, "map_dac", false, mn_bucket(M, N), 0, bl);
+  if (best) {
+    memset(best, 0, sizeof(*best));
+    best->algo = RS_MAP_DAC;
+    best->leaf_L = bl;
   }
   return RS_OK;
 }
@@ -827,8 +1086,20 @@ rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off,
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s) return s;
-  h->tuned_threads = bt;
-  h->tuned_leaf = bl;
+  {
+    long long sM = 0, sN = 0;
+    if (h_w_off && h_r_off) {
+      sM = h_w_off[K];
+      sN = h_r_off[K];
+    } else {
+      int64_t t[2] = {0, 0};
+      RS_CK(h, cudaMemcpy(&t[0], w_off + K, sizeof(int64_t), cudaMemcpyDeviceToHost));
+      RS_CK(h, cudaMemcpy(&t[1], r_off + K, sizeof(int64_t), cudaMemcpyDeviceToHost));
+      sM = t[0];
+      sN = t[1];
+    }
+    set_tune(h, "batched", o.prec == RS_F32_COMP, mn_bucket(sM, sN), bt, bl);
+  }
   if (best) {
     memset(best, 0, sizeof(*best));
     best->prec = o.prec;

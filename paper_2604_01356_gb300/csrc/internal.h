@@ -87,6 +87,13 @@ cudaError_t launch_uniform_scan(bool f32, long long ndraw, unsigned long long se
                                 void* Z, void* Ztot, PathConsts* consts, void* desc, unsigned* ctr, int* status,
                                 int spin_limit, bool withhold_first, cudaStream_t st, int scheme = 0);
 cudaError_t launch_uniform_norm(long long N, const void* Z, const PathConsts* consts, double* U, cudaStream_t st);
+// Up to kUSmallMaxN samples (one step of the CTA's 2048 draws): the spacing
+// scan and U = Z / Z_{N+1} by one CTA in one launch (no cleared workspace); Z
+// and U identical to the two above.  Beyond one step the multi-tile scan is
+// faster.
+constexpr long long kUSmallMaxN = 2047;
+cudaError_t launch_uniform_small(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,
+                                 double* U, cudaStream_t st, int scheme);
 cudaError_t launch_philox(unsigned long long seed, unsigned long long inst, unsigned long long first, long long n,
                           unsigned long long* out, cudaStream_t st);
 
@@ -146,9 +153,14 @@ constexpr int kBMaxSeg = 512;     // segments of the largest instance a CTA take
 constexpr int kBMaxN = 2048;      // samples of the largest instance a CTA takes
 constexpr int kSortMax = 16384;   // batches up to this size are ordered by M_k on the device
 cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cudaStream_t st);
-cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
-                               unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st, int scheme, const LogTab* tab);
+// f32: binary32 weights and draws, else binary64.  w_off == nullptr: the one
+// instance (M0, N0); queue == nullptr: CTA b takes instance b (launch K
+// CTAs); order == nullptr: identity order.  Instance k draws from the Philox
+// stream (seed, inst_base + k).
+cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, const long long* r_off, const int* order,
+                           int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
+                           int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
+                           const LogTab* tab);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

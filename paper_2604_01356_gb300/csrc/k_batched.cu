@@ -27,7 +27,7 @@
 //
 // Instances with more than kBMaxSeg segments or kBMaxN samples are not
 // processed here (the host sends them through the single-instance path).
-#include "seg_common.cuh"
+#include "map_common.cuh"
 
 // Phase timestamps (profiling builds only, -DGBR_PHASE_STAMPS): %globaltimer
 // at the phase ends of the first instance each CTA takes, 8 slots per CTA,
@@ -104,16 +104,21 @@ __device__ __noinline__ void compute_c(xf* dst, u128 S, u128 Ztot) {
 
 }  // namespace
 
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restrict__ w,
-                                                          const long long* __restrict__ w_off,
-                                                          const long long* __restrict__ r_off,
-                                                          const int* __restrict__ order, int K,
-                                                          unsigned long long seed, int leaf_T,
-                                                          int* __restrict__ out, unsigned* queue, int* status,
-                                                          int scheme, const LogTab* __restrict__ tab) {
-  using Tr = FixedTraits<float>;
-  using Bits = Tr::Bits;
+// T: the weight type (binary32 weights with binary32 draws, or binary64 with
+// binary64 draws).  With w_off == nullptr the batch is the single instance
+// (M0, N0); with queue == nullptr CTA b takes instance b only (no queue to
+// clear); order == nullptr is the identity order.  Instance k draws from the
+// Philox stream (seed, inst_base + k).
+template <typename T, int kThreads>
+__global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, const long long* __restrict__ w_off,
+                                                      const long long* __restrict__ r_off,
+                                                      const int* __restrict__ order, int K, unsigned long long seed,
+                                                      unsigned long long inst_base, long long M0, long long N0,
+                                                      int leaf_T, int* __restrict__ out, unsigned* queue,
+                                                      int* status, int scheme, const LogTab* __restrict__ tab) {
+  using Tr = FixedTraits<T>;
+  using Bits = typename Tr::Bits;
+  constexpr bool F32 = sizeof(T) == 4;
   constexpr int kWarps = kThreads / 32;
   constexpr int kChunk = kThreads * 4;  // draws per block per chunk (4 per thread)
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -125,22 +130,29 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
     sm.tab.invc[i] = tab->invc[i];
   }
   bool first = true;
+  int taken = 0;  // instances this CTA has taken (without a queue: one)
   GBR_BSTAMP(true, 0);
   while (true) {
     __syncthreads();  // the previous instance is done with shared memory
-    if (tid == 0) sm.item = (int)atomicAdd(queue, 1u);
+    if (queue) {
+      if (tid == 0) sm.item = (int)atomicAdd(queue, 1u);
+    } else if (tid == 0) {
+      sm.item = taken ? K : (int)blockIdx.x;
+    }
+    ++taken;
     __syncthreads();
     const int item = sm.item;
     if (item >= K) break;
-    const int k = order[item];
-    const long long wb = w_off[k];
-    const long long Mk = w_off[k + 1] - wb;
-    const long long rb = r_off[k];
-    const long long Nk = r_off[k + 1] - rb;
+    const int k = order ? order[item] : item;
+    const long long wb = w_off ? w_off[k] : 0;
+    const long long Mk = w_off ? w_off[k + 1] - wb : M0;
+    const long long rb = r_off ? r_off[k] : 0;
+    const long long Nk = r_off ? r_off[k + 1] - rb : N0;
     if (Nk <= 0 || Mk <= 0) continue;
     const long long nseg = (Mk + kSeg - 1) / kSeg;
     if (nseg > kBMaxSeg || Nk > kBMaxN) continue;  // left to the single-instance path
-    const float* wk = w + wb;
+    const unsigned long long inst = inst_base + (unsigned long long)k;
+    const T* wk = w + wb;
     const bool vec = (reinterpret_cast<uintptr_t>(wk) & 15) == 0;
     int* outk = out + rb;
 
@@ -151,22 +163,22 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
       const int s1 = s0 + kWarps;
       Bits b0[kSegV], b1[kSegV];
       if (vec) {
-        load_seg_striped<float, true>(wk, (long long)s0 * kSeg, Mk, lane, b0);
-        if (s1 < nseg) load_seg_striped<float, true>(wk, (long long)s1 * kSeg, Mk, lane, b1);
+        load_seg_striped<T, true>(wk, (long long)s0 * kSeg, Mk, lane, b0);
+        if (s1 < nseg) load_seg_striped<T, true>(wk, (long long)s1 * kSeg, Mk, lane, b1);
       } else {
-        load_seg_striped<float, false>(wk, (long long)s0 * kSeg, Mk, lane, b0);
-        if (s1 < nseg) load_seg_striped<float, false>(wk, (long long)s1 * kSeg, Mk, lane, b1);
+        load_seg_striped<T, false>(wk, (long long)s0 * kSeg, Mk, lane, b0);
+        if (s1 < nseg) load_seg_striped<T, false>(wk, (long long)s1 * kSeg, Mk, lane, b1);
       }
       uint64_t F;
       uint32_t E;
-      seg_sum_bits<float>(b0, lane, status, F, E);
+      seg_sum_bits<T>(b0, lane, status, F, E);
       if (lane == 0) {
         sm.F[s0] = F;
         sm.E[s0] = (int)E;
       }
       em = max(em, (int)E);
       if (s1 < nseg) {
-        seg_sum_bits<float>(b1, lane, status, F, E);
+        seg_sum_bits<T>(b1, lane, status, F, E);
         if (lane == 0) {
           sm.F[s1] = F;
           sm.E[s1] = (int)E;
@@ -179,6 +191,7 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
     int Emax = 0;
 #pragma unroll
     for (int i = 0; i < kWarps; ++i) Emax = max(Emax, sm.emax_w[i]);
+    const long long ge = (long long)Emax - Tr::kBias - Tr::kShift - kGridHead;  // grid exponent
 
     GBR_BSTAMP(first, 2);
     // ---- B: grid prefixes (consecutive segments per thread) -----------------
@@ -214,9 +227,9 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
     for (long long d0 = 0; d0 < ndraw; d0 += kChunk) {
       const long long k0 = d0 + 4LL * tid;  // one Philox block per thread
       uint64_t wd[4];
-      philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, (uint64_t)k, wd);
+      philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
       u128 f[4];
-      block_spacings<true>(scheme, k0, ndraw, seed, (unsigned long long)k, wd, &sm.tab, f);
+      block_spacings<F32>(scheme, k0, ndraw, seed, inst, wd, &sm.tab, f);
       u128 run = {0ULL, 0ULL}, inc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -292,14 +305,14 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
 #pragma unroll
           for (int q = 0; q < kSegV; ++q) b[q] = bn[q];
         } else if (vec) {
-          load_seg_blocked<float, true>(wk, (long long)sc * kSeg, Mk, lane, b);
+          load_seg_blocked<T, true>(wk, (long long)sc * kSeg, Mk, lane, b);
         } else {
-          load_seg_blocked<float, false>(wk, (long long)sc * kSeg, Mk, lane, b);
+          load_seg_blocked<T, false>(wk, (long long)sc * kSeg, Mk, lane, b);
         }
         pf = -1;
-        if (sc + 1 < sb) {  // the next segment's weights travel while this one is resolved
-          if (vec) load_seg_blocked<float, true>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
-          else load_seg_blocked<float, false>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+        if (F32 && sc + 1 < sb) {  // the next segment's weights travel while this one is resolved
+          if (vec) load_seg_blocked<T, true>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+          else load_seg_blocked<T, false>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
           pf = sc + 1;
         }
         const uint32_t E = (uint32_t)sm.E[sc];
@@ -308,8 +321,17 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
         const int sh = (int)E - Emax + kGridHead;
         const long long rem_len = Mk - (long long)sc * kSeg;
         const int len = (int)(rem_len < kSeg ? rem_len : kSeg);
+        // a head segment (binary64 weights): the prefix before it is too
+        // small for the segment grid to decide every key exactly; a key that
+        // lies within the grid's truncation of a prefix is decided by exact
+        // per-element sums scaled to the key (as on the single-instance path)
+        bool head = false;
+        if (!F32) {
+          const xf Px = xf_make(Ps.hi, Ps.lo, 0);
+          head = xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50;
+        }
         uint64_t pref[kSegV];
-        seg_prefixes<float>(b, E, lane, pref);
+        seg_prefixes<T>(b, E, lane, pref);
         if (ie - i <= leaf_T) {
           // a few samples: a warp-wide count over the prefixes in registers
           // (the linear-walk leaf)
@@ -323,6 +345,30 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
             for (int q = 0; q < kSegV; ++q) cnt += pref[q] < Kq ? 1 : 0;
 #pragma unroll
             for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+            if (head) {  // warp-uniform: every lane holds the same key
+              const xf rx = xf_make(rem.hi, rem.lo, 0);
+              if (xf_zero(rx) || rx.e + kXfTop < (long long)sh + 50) {
+                bool amb;
+                if (Kq >= Fs) {
+                  amb = true;
+                } else if ((long long)Kq <= len) {
+                  amb = cnt > 0;
+                } else {
+                  int c2 = 0;
+#pragma unroll
+                  for (int q = 0; q < kSegV; ++q) c2 += pref[q] < Kq - (unsigned long long)len ? 1 : 0;
+#pragma unroll
+                  for (int o = 16; o; o >>= 1) c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
+                  amb = c2 != cnt;
+                }
+                if (amb) {
+                  cnt = vec ? head_count<true>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                xf_make(rem.hi, rem.lo, ge), lane)
+                            : head_count<false>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                 xf_make(rem.hi, rem.lo, ge), lane);
+                }
+              }
+            }
             if (lane == 0) {
               const int jj = cnt < len ? cnt : len - 1;
               long long idx = (long long)sc * kSeg + jj;
@@ -339,12 +385,41 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
 #pragma unroll 1
           for (long long j0 = i; j0 < ie; j0 += 32) {
             const long long j = j0 + lane;
-            if (j < ie) {
+            const bool mine = j < ie;
+            u128 rem = {0ULL, 0ULL};
+            unsigned long long Kq = 1;
+            int cnt = 0;
+            if (mine) {
               const u128 key = j0 == i ? kl : sm.key[j];
-              const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
-              const unsigned long long Kq = ceil_units(rem, sh, Fs);
-              const int lo = count_below(sp, Kq);
-              const int jj = lo < len ? lo : len - 1;
+              rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
+              Kq = ceil_units(rem, sh, Fs);
+              cnt = count_below(sp, Kq);
+            }
+            if (head) {  // warp-uniform branch; the ambiguous keys one by one
+              bool amb = false;
+              if (mine) {
+                const xf rx = xf_make(rem.hi, rem.lo, 0);
+                if (xf_zero(rx) || rx.e + kXfTop < (long long)sh + 50) {
+                  if (Kq >= Fs) amb = true;
+                  else if ((long long)Kq <= len) amb = cnt > 0;
+                  else amb = count_below(sp, Kq - (unsigned long long)len) != cnt;
+                }
+              }
+              unsigned gx = __ballot_sync(0xFFFFFFFFu, amb);
+#pragma unroll 1
+              while (gx) {
+                const int jl = __ffs(gx) - 1;
+                gx &= gx - 1;
+                const u128 rj = shfl_v(rem, jl);
+                const int cj = vec ? head_count<true>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                      xf_make(rj.hi, rj.lo, ge), lane)
+                                   : head_count<false>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                       xf_make(rj.hi, rj.lo, ge), lane);
+                if (lane == jl) cnt = cj;
+              }
+            }
+            if (mine) {
+              const int jj = cnt < len ? cnt : len - 1;
               long long idx = (long long)sc * kSeg + jj;
               if (idx > Mk - 1) idx = Mk - 1;
               outk[j] = (int)idx;
@@ -360,34 +435,57 @@ __global__ void __launch_bounds__(kThreads) k_batched_f32(const float* __restric
   }
 }
 
-template <int kThreads>
-static cudaError_t batched_t(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
-                             unsigned long long seed, int leaf_T, int* out, unsigned* queue, int* status,
-                             cudaStream_t st, int scheme, const LogTab* tab) {
+template <typename T, int kThreads>
+static cudaError_t batched_t(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
+                             unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
+                             int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
+                             const LogTab* tab) {
   const size_t smem = sizeof(BatchSmem<kThreads / 32>);
-  cudaError_t e = cudaFuncSetAttribute(k_batched_f32<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_batched<T, kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_f32<kThreads>, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  long long blocks = (long long)num_sms() * per_sm;
-  if (blocks > K) blocks = K;
+  long long blocks = K;
+  if (queue) {
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<T, kThreads>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    blocks = (long long)num_sms() * per_sm;
+    if (blocks > K) blocks = K;
+  }
   if (blocks < 1) blocks = 1;
-  k_batched_f32<kThreads><<<(unsigned)blocks, kThreads, smem, st>>>(w, w_off, r_off, order, K, seed, leaf_T, out,
-                                                                     queue, status, scheme, tab);
+  k_batched<T, kThreads><<<(unsigned)blocks, kThreads, smem, st>>>(w, w_off, r_off, order, K, seed, inst_base, M0, N0,
+                                                                    leaf_T, out, queue, status, scheme, tab);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batched_f32(const float* w, const long long* w_off, const long long* r_off, const int* order, int K,
-                               unsigned long long seed, int threads, int leaf_T, int* out, unsigned* queue,
-                               int* status, cudaStream_t st, int scheme, const LogTab* tab) {
-  if (K <= 0) return cudaSuccess;
+template <typename T>
+static cudaError_t batched_dispatch(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
+                                    unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
+                                    int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st,
+                                    int scheme, const LogTab* tab) {
   switch (threads) {
-    case 128: return batched_t<128>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
-    case 512: return batched_t<512>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
-    default: return batched_t<256>(w, w_off, r_off, order, K, seed, leaf_T, out, queue, status, st, scheme, tab);
+    case 128:
+      return batched_t<T, 128>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
+                               scheme, tab);
+    case 512:
+      return batched_t<T, 512>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
+                               scheme, tab);
+    default:
+      return batched_t<T, 256>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
+                               scheme, tab);
   }
+}
+
+cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, const long long* r_off, const int* order,
+                           int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
+                           int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
+                           const LogTab* tab) {
+  if (K <= 0) return cudaSuccess;
+  if (f32)
+    return batched_dispatch<float>(static_cast<const float*>(w), w_off, r_off, order, K, seed, inst_base, M0, N0,
+                                   threads, leaf_T, out, queue, status, st, scheme, tab);
+  return batched_dispatch<double>(static_cast<const double*>(w), w_off, r_off, order, K, seed, inst_base, M0, N0,
+                                  threads, leaf_T, out, queue, status, st, scheme, tab);
 }
 
 // ---- work order: instances by M_k descending (ties by index) ----------------

@@ -51,6 +51,80 @@ __global__ void __launch_bounds__(256) k_uniform_norm(long long N, const u128* _
   }
 }
 
+// Small N: the whole of Algorithm 1 by one CTA, one launch and no cleared
+// workspace: 512 threads x 4 draws per step (one Philox block per thread),
+// spacings on the 2^-88 grid, an exact 128-bit block scan carried across
+// steps, then 1/Z_{N+1} (recip_total, as the multi-tile scan stores it) and
+// U_i = Z_i / Z_{N+1} rounded as k_uniform_norm does.  The integers are those
+// of the multi-tile scan, so Z and U are identical to it.
+constexpr int kUSmallThreads = 512;
+template <bool F32>
+__global__ void __launch_bounds__(kUSmallThreads) k_uniform_small(long long ndraw, unsigned long long seed,
+                                                                  unsigned long long inst, u128* __restrict__ Z,
+                                                                  double* __restrict__ U, int scheme) {
+  constexpr int kW = kUSmallThreads / kWarp;
+  __shared__ LogTab tab;
+  __shared__ u128 wsum[kW];
+  __shared__ xf s_r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 129; i += kUSmallThreads) {
+    tab.nlogc[i] = g_logtab.nlogc[i];
+    tab.invc[i] = g_logtab.invc[i];
+  }
+  __syncthreads();
+  const long long N = ndraw - 1;
+  u128 carry = {0ULL, 0ULL};
+#pragma unroll 1
+  for (long long d0 = 0; d0 < ndraw; d0 += 4LL * kUSmallThreads) {
+    const long long k0 = d0 + 4LL * tid;
+    uint64_t words[4];
+    philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, words);
+    u128 f[4], inc[4];
+    block_spacings<F32>(scheme, k0, ndraw, seed, inst, words, &tab, f);
+    u128 run = {0ULL, 0ULL};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      run = u128_add(run, f[q]);
+      inc[q] = run;
+    }
+    const u128 incl = warp_incl_scan_v(run, lane);
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    u128 off = {0ULL, 0ULL}, tot = {0ULL, 0ULL};
+#pragma unroll
+    for (int i = 0; i < kW; ++i) {
+      const u128 x = wsum[i];
+      if (i < warp) off = u128_add(off, x);
+      tot = u128_add(tot, x);
+    }
+    __syncthreads();  // wsum is reused by the next step
+    off = u128_add(carry, u128_add(off, u128_sub(incl, run)));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (k0 + q < N) Z[k0 + q] = u128_add(off, inc[q]);
+    carry = u128_add(carry, tot);
+  }
+  if (tid == 0) s_r = u128_is_zero(carry) ? lb_zero<xf>() : recip_total(carry);
+  __syncthreads();
+  const xf r = s_r;
+#pragma unroll 1
+  for (long long i = tid; i < N; i += kUSmallThreads) {
+    long long ub = (long long)xf_to_f64_bits(xf_mul_u128(r, Z[i]));
+    if (ub > 0x3FF0000000000000LL) ub = 0x3FF0000000000000LL;
+    U[i] = __longlong_as_double(ub);
+  }
+}
+
+cudaError_t launch_uniform_small(bool f32, long long ndraw, unsigned long long seed, unsigned long long inst, void* Z,
+                                 double* U, cudaStream_t st, int scheme) {
+  if (ndraw <= 1) return cudaSuccess;
+  if (f32)
+    k_uniform_small<true><<<1, kUSmallThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, U, scheme);
+  else
+    k_uniform_small<false><<<1, kUSmallThreads, 0, st>>>(ndraw, seed, inst, (u128*)Z, U, scheme);
+  return cudaGetLastError();
+}
+
 __global__ void k_philox_words(unsigned long long seed, unsigned long long inst, unsigned long long first, long long n,
                                unsigned long long* __restrict__ out) {
   const long long stride = (long long)gridDim.x * blockDim.x;

@@ -1,8 +1,8 @@
 """GPU: the batched persistent path (many instances in one launch).
 
-Its indices must equal, bit for bit, those of rs_resample_w run on each
-instance alone (same binary32 precision): both use the same exact integer
-arithmetic.  The per-instance path is itself checked against the oracle in
+Its indices must equal, bit for bit, those of rs_resample_w's multi-kernel
+path run on each instance alone (same precision, binary32 or binary64): both
+use the same exact integer arithmetic.  The per-instance path is itself checked against the oracle in
 test_gpu_parity; here the batched result is also checked against the oracle
 directly on a small batch.
 """
@@ -59,7 +59,10 @@ def _mixed_batch(seed):
     return w, woff, roff
 
 
-def _per_instance(g, h, w, woff, roff, seed):
+def _per_instance(g, h, w, woff, roff, seed, prec=None):
+    """Every instance through rs_resample_w's multi-kernel path (debug bit
+    1), which shares no kernel with the persistent one."""
+    prec = g.RS_F32_COMP if prec is None else prec
     K = len(woff) - 1
     out = torch.empty(max(int(roff[-1]), 1), dtype=torch.int32, device="cuda")
     wd = dev(w)
@@ -69,19 +72,43 @@ def _per_instance(g, h, w, woff, roff, seed):
             continue
         wk = wd[int(woff[k]):int(woff[k + 1])]
         ok = out[int(roff[k]):int(roff[k + 1])]
-        g.rs_resample_w(h.h, wk, Mk, Nk, seed, k, ok, None, g.opts(prec=g.RS_F32_COMP))
+        g.rs_resample_w(h.h, wk, Mk, Nk, seed, k, ok, None, g.opts(prec=prec, debug_flags=2))
     assert h.status() == g.RS_OK
     return host(out)[: int(roff[-1])]
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("threads", [128, 256, 512])
 @pytest.mark.parametrize("leaf", [1, 4, 32])
-def test_batched_equals_per_instance_bit_exact(g, h, threads, leaf):
+def test_batched_equals_per_instance_bit_exact(g, h, threads, leaf, prec):
     w, woff, roff = _mixed_batch(11)
-    ref = _per_instance(g, h, w, woff, roff, seed=5)
+    p = g.RS_F32_COMP if prec == "f32" else g.RS_F64
+    if prec == "f64":
+        w = w.astype(np.float64)
+    ref = _per_instance(g, h, w, woff, roff, seed=5, prec=p)
     out = torch.full((int(roff[-1]),), -1, dtype=torch.int32, device="cuda")
     g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), len(woff) - 1, 5, out, woff, roff,
-                          g.opts(prec=g.RS_F32_COMP, tile_threads=threads, leaf_L=leaf))
+                          g.opts(prec=p, tile_threads=threads, leaf_L=leaf))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(host(out), ref)
+
+
+@pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
+def test_batched_f64_adversarial_heads(g, h, kind):
+    """Binary64 weights through the persistent kernel: adversarial weight
+    vectors (zero runs, ties, a spike, tiny/huge/wide dynamic ranges) whose
+    head segments need the exact per-element decision, against the
+    multi-kernel path on each instance."""
+    Mk = [4096, 513, 20_000, 1, 777]
+    Nk = [1000, 513, 2048, 5, 300]
+    woff = np.zeros(len(Mk) + 1, dtype=np.int64)
+    roff = np.zeros(len(Mk) + 1, dtype=np.int64)
+    np.cumsum(Mk, out=woff[1:])
+    np.cumsum(Nk, out=roff[1:])
+    w = np.concatenate([workloads.adversarial_weights(kind, m, seed=i) for i, m in enumerate(Mk)])
+    ref = _per_instance(g, h, w, woff, roff, seed=21, prec=g.RS_F64)
+    out = torch.full((int(roff[-1]),), -1, dtype=torch.int32, device="cuda")
+    g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), len(Mk), 21, out, woff, roff, g.opts(prec=g.RS_F64))
     assert h.status() == g.RS_OK
     assert np.array_equal(host(out), ref)
 

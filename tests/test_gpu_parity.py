@@ -84,6 +84,24 @@ def test_sorted_uniform_f32_comp(g, h, N):
     assert np.max(np.abs(got - ref) / ref) <= REL_U_F32  # what the path achieves
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", ["multinomial", "stratified", "systematic"])
+@pytest.mark.parametrize("N", [1, 2, 1023, 1024, 2046, 2047, 2048])
+def test_sorted_uniform_one_cta_equals_lookback(g, h, prec, scheme, N):
+    """Up to 2,047 samples the sorted uniforms come from one CTA in one
+    launch; they must equal, bit for bit, those of the multi-tile look-back
+    scan (debug bit 2 forces it)."""
+    p = g.RS_F32_COMP if prec == "f32" else g.RS_F64
+    sc = {"multinomial": g.RS_SCHEME_MULTINOMIAL, "stratified": g.RS_SCHEME_STRATIFIED,
+          "systematic": g.RS_SCHEME_SYSTEMATIC}[scheme]
+    a = torch.empty(N, dtype=torch.float64, device="cuda")
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    g.rs_sorted_uniform(h.h, N, 31, 2, a, g.opts(prec=p, scheme=sc))
+    g.rs_sorted_uniform(h.h, N, 31, 2, b, g.opts(prec=p, scheme=sc, debug_flags=4))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(host(a).view(np.int64), host(b).view(np.int64))
+
+
 # ----------------------------------------------------- cumulative (Eq.3) --
 SIZES = [1, 2, 511, 512, 513, 4095, 4096, 4097, 37 * 4096 + 123]
 
@@ -326,7 +344,7 @@ def test_host_argument_errors(g, h):
 
 # -------------------------------------------------------------- tracing ----
 def test_tracing_outside_capture_reports_kernels(g, h):
-    w = workloads.weights_lognormal(100_000, 2.0, seed=4)
+    w = workloads.weights_lognormal(300_000, 2.0, seed=4)
     out = torch.empty(500, dtype=torch.int32, device="cuda")
     wd = dev(w)
     g.rs_trace_enable(h.h, True)
@@ -334,24 +352,30 @@ def test_tracing_outside_capture_reports_kernels(g, h):
         for _ in range(3):
             g.rs_resample_w(h.h, wd, w.size, 500, 1, 0, out)  # one cooperative launch
             g.rs_resample_w(h.h, wd, w.size, 500, 1, 0, out, None, g.opts(debug_flags=2))  # multi-kernel
+            g.rs_resample_w(h.h, wd, 20_000, 500, 1, 0, out)  # a small instance: one CTA
         g.rs_trace_collect(h.h)
         rep = g.rs_trace_report(h.h)
     finally:
         g.rs_trace_enable(h.h, False)
         g.rs_trace_reset(h.h)
     assert h.status() == g.RS_OK
-    for name in ("fused", "w_reduce", "seg_prefix", "uniform_scan", "map_seg"):
+    for name in ("fused", "w_reduce", "seg_prefix", "uniform_scan", "map_seg", "single_cta"):
         n, ms = rep[name]
         assert n == 3 and ms > 0.0, (name, rep[name])
 
 
 # ------------------------------------ fused launch vs multi-kernel path ----
-FUSED_CASES = [(1, 1), (2, 5), (513, 1000), (9 * 4096 + 5, 4097), (300_000, 64), (1_000_003, 300_001)]
+FUSED_CASES = [(1, 1), (2, 5), (513, 1000), (4096, 1024), (131_072, 2048), (9 * 4096 + 5, 4097), (300_000, 64),
+               (1_000_003, 300_001), (4_000_000, 4000)]
 
 
+@pytest.mark.parametrize("path", ["auto", "cooperative"])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("M,N", FUSED_CASES)
-def test_fused_equals_multikernel(g, h, prec, M, N):
+def test_fused_equals_multikernel(g, h, prec, M, N, path):
+    """The one-launch forms of rs_resample_w (the one-CTA path of small
+    instances, and the cooperative launch, forced with debug bit 2) against
+    the multi-kernel path, index for index."""
     w = workloads.weights_lognormal(M, 2.0, seed=M)
     p = g.RS_F64 if prec == "f64" else g.RS_F32_COMP
     if prec == "f32":
@@ -359,7 +383,7 @@ def test_fused_equals_multikernel(g, h, prec, M, N):
     wd = dev(w)
     a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
     b = torch.full((N,), -2, dtype=torch.int32, device="cuda")
-    g.rs_resample_w(h.h, wd, M, N, 9, 2, a, None, g.opts(prec=p))
+    g.rs_resample_w(h.h, wd, M, N, 9, 2, a, None, g.opts(prec=p, debug_flags=0 if path == "auto" else 4))
     g.rs_resample_w(h.h, wd, M, N, 9, 2, b, None, g.opts(prec=p, debug_flags=2))
     assert h.status() == g.RS_OK
     assert np.array_equal(host(a), host(b))
@@ -391,8 +415,10 @@ def test_fused_draw_split_modes(g, h, prec, which):
 
 
 @pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
-def test_fused_equals_multikernel_adversarial(g, h, kind):
-    M, N = 7 * 4096 + 3, 5000
+@pytest.mark.parametrize("M,N", [(7 * 4096 + 3, 5000), (7 * 4096 + 3, 2000)])
+def test_fused_equals_multikernel_adversarial(g, h, kind, M, N):
+    """Adversarial weights on the cooperative launch (N = 5000) and on the
+    one-CTA path of small instances (N = 2000) against the multi-kernel path."""
     w = workloads.adversarial_weights(kind, M, seed=4)
     wd = dev(w)
     a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
