@@ -64,13 +64,23 @@ def test_static_size_limit_and_arguments(g):
 
 
 def test_static_repeated_calls_keep_free_memory(g):
+    """Twenty calls after the set-up call leave the device's free memory
+    unchanged.  The reading is device-wide, so another process allocating
+    meanwhile could move it: the measurement is repeated (up to three
+    times) and one unchanged reading suffices, while an entry point that
+    allocated per call would lower every one of them."""
     N = 4096
     U = torch.empty(N, dtype=torch.float64, device="cuda")
     assert g.rs_sorted_uniform_static(N, 3, 1, U) == g.RS_OK  # set-up on this device
     torch.cuda.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    for k in range(20):
-        assert g.rs_sorted_uniform_static(N, 3 + k, 1, U) == g.RS_OK
-    torch.cuda.synchronize()
-    free1, _ = torch.cuda.mem_get_info()
-    assert free1 == free0
+    deltas = []
+    for attempt in range(3):
+        free0, _ = torch.cuda.mem_get_info()
+        for k in range(20):
+            assert g.rs_sorted_uniform_static(N, 3 + k, 1, U) == g.RS_OK
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        deltas.append(free0 - free1)
+        if free1 == free0:
+            break
+    assert deltas[-1] == 0, deltas
