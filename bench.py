@@ -514,6 +514,24 @@ def _time_calls(fn, stream, reps, warm=2):
     return e0.elapsed_time(e1) / reps
 
 
+def _time_graph_calls(fn, stream, calls=64, reps=10):
+    """Device time per call: `calls` back-to-back calls captured as one CUDA
+    graph, replayed `reps` times (host issue cost amortised)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            fn(stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        for _ in range(calls):
+            fn(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ms = _time_calls(graph.replay, stream, reps)
+    del graph
+    return ms / calls
+
+
 def batched_measure(g, h, dev, stream, hbm, reps=20):
     """8192 EnGMF-shaped instances (N_k ~ U{64..2048}, P_k ~ U{1..64},
     M_k = N_k P_k, binary32 weights): the persistent batched launch (autotuned,
@@ -648,14 +666,22 @@ def small_measure(g, h, dev, stream, reps=200):
     wd = torch.from_numpy(wl.w).to(dev)
     W = torch.from_numpy(oracle.cumulative(wl.w)[0]).to(dev)
     out = torch.empty(N, dtype=torch.int32, device=dev)
-    res = {"M": M, "N": N, "bytes": 8 * M + 4 * N}
-    ms = _time_calls(lambda: g.rs_resample_w(h.h, wd, M, N, seed, 0, out, stream=stream), stream, reps)
+    res = {"M": M, "N": N, "bytes": 8 * M + 4 * N,
+           "timing": "*_us_per_call: back-to-back calls from Python (includes the host's issue cost per call); "
+                     "*_graph_us_per_call: 64 calls captured as one CUDA graph (device time per call)"}
+    whole = lambda s: g.rs_resample_w(h.h, wd, M, N, seed, 0, out, stream=s)  # noqa: E731
+    ms = _time_calls(lambda: whole(stream), stream, reps)
     res["whole_path_us_per_call"] = ms * 1e3
     res["whole_path_particles_per_s"] = N / (ms * 1e-3)
+    ms = _time_graph_calls(whole, stream)
+    res["whole_path_graph_us_per_call"] = ms * 1e3
+    res["whole_path_graph_particles_per_s"] = N / (ms * 1e-3)
     for name, algo in [("dac", g.RS_MAP_DAC), ("binary", g.RS_MAP_BINARY), ("linear", g.RS_MAP_LINEAR)]:
         o = g.opts(algo=algo)
-        ms = _time_calls(lambda: g.rs_resample_W(h.h, W, M, N, seed, 0, out, o, stream=stream), stream, reps)
+        mapf = lambda s, o=o: g.rs_resample_W(h.h, W, M, N, seed, 0, out, o, stream=s)  # noqa: E731
+        ms = _time_calls(lambda: mapf(stream), stream, reps)
         res["map_only_us_per_call_" + name] = ms * 1e3
+        res["map_only_graph_us_per_call_" + name] = _time_graph_calls(mapf, stream) * 1e3
     if h.status() != g.RS_OK:
         raise RuntimeError("device status after the small workload")
     return res

@@ -105,7 +105,7 @@ typedef struct {
                           the multi-kernel path instead of the single cooperative
                           launch (identical results; for comparison).  Bit 2: the
                           one-CTA paths of small instances (rs_resample_w up to
-                          32,768 weights and 2,048 samples; the sorted uniforms of
+                          32,768 weights and 2,048 samples, both forms; the sorted uniforms of
                           rs_sorted_uniform and rs_resample_W up to 2,047
                           samples) are not taken (identical results; for
                           comparison).  Bit 0 also keeps the uniforms on the
@@ -128,10 +128,13 @@ rs_status rs_destroy(rs_handle* h);
  *  out_idx [N] int32 sample indices, written.
  *  W_out   [M] binary64 cumulative weights W (Eq. 3), written if not NULL.
  *  seed, instance select the Philox stream of the N+1 draws.
- * Launch forms, all giving identical indices: an instance of at most 32,768
- * weights and 2,048 samples runs on one CTA (one launch); otherwise one
- * cooperative launch of one CTA per SM (a multi-kernel sequence when the
- * device cannot hold that grid, or when W_out is requested).  The map is the
+ * Launch forms, all giving identical indices: an instance of at most 12,288
+ * weights and 2,047 samples runs on one CTA with its weights staged in
+ * shared memory; one of at most 32,768
+ * weights and 2,048 samples on one CTA reading them from global memory
+ * (one launch each); otherwise one cooperative launch of one CTA per SM (a
+ * multi-kernel sequence when the device cannot hold that grid, or when W_out
+ * is requested).  The map is the
  * segmented divide and conquer (exact segment sums and their prefixes, the
  * segment of each key, the element from that segment's exact prefixes);
  * opts->algo is ignored here. */

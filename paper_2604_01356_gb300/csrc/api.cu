@@ -759,6 +759,14 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   if (W_out && !aligned(W_out, 8)) return fail(h, RS_EINVAL, "W_out must be 8-byte aligned");
   if (N == 0 && !W_out) return RS_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (N > 0 && !W_out && !(o.debug & 6) && M <= kSmallMaxM && N <= kSmallMaxN) {
+    // a small instance: the whole path on one CTA, the weights staged in
+    // shared memory
+    RS_TRACE(h, "small_smem", st);
+    RS_CK(h, launch_small(f32, w, M, N, seed, instance, out_idx, h->status, st, o.scheme,
+                          static_cast<const LogTab*>(h->logtab)));
+    return RS_OK;
+  }
   if (N > 0 && !W_out && !(o.debug & 6) && M <= kSmallM && N <= kBMaxN) {
     // a small instance: the whole path on one CTA
     RS_TRACE(h, "single_cta", st);

@@ -161,6 +161,15 @@ cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, cons
                            int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
                            int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
                            const LogTab* tab);
+// --- one-CTA whole path of a small instance, weights staged in shared memory
+// (512 threads; N + 1 <= 2048 draws in one tile; at most kSmallMaxM
+// weights).  Indices equal those of every other form of rs_resample_w.
+constexpr int kSmThreads = 512;
+constexpr long long kSmallMaxN = 2047;
+constexpr long long kSmallMaxM = 12288;
+size_t small_smem_bytes(bool f32);
+cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,
+                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

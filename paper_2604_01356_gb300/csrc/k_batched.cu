@@ -435,6 +435,284 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
   }
 }
 
+// ---- the whole path of a small instance on one CTA, weights in shared memory
+// (at most 12,288 weights, N <= 2047).  Latency is what counts here, so the
+// two independent chains overlap and nothing is done twice:
+//   - the weights travel to shared memory by asynchronous copies while the
+//     draws are made (all N + 1 in one tile over the 512 threads);
+//   - then warp 15 computes 1 / Z_{N+1} while warps 0-14 take one segment
+//     each: its exact sum (Eq. 3 at the segment level) and its exact
+//     in-segment prefixes, written once to shared memory (in place of
+//     binary64 weights);
+//   - the grid prefixes, c, the keys, and the map: warp w takes samples
+//     [N w / 16, N (w+1) / 16) in rounds of 32, finds each sample's segment
+//     by a binary search over the grid prefixes (keys are sorted) and the
+//     element by a binary search over that segment's staged prefixes, as the
+//     persistent kernel's search leaf does; so the indices are identical.
+template <typename T>
+struct SmallSmem {
+  static constexpr int kMaxSeg = kSmallMaxM / kSeg;
+  u128 key[kSmallMaxN + 1];                    // Z_i, then the keys
+  alignas(16) unsigned long long P[kSmallMaxM];  // binary64 weights, then every segment's exact prefixes
+  alignas(16) uint32_t w32[sizeof(T) == 4 ? kSmallMaxM : 4];  // binary32 weights
+  u128 pre[kMaxSeg + 1];
+  unsigned long long F[kMaxSeg];
+  int E[kMaxSeg];
+  u128 wsum[kSmThreads / 32];
+  xf c, invZ;
+  int emax_w[kSmThreads / 32];
+  LogTab tab;
+};
+
+// Shared-memory position of entry e of an array of 8-byte (kPer = 2) or
+// 4-byte (kPer = 4) entries: 16-byte chunks are swizzled within each
+// 128-byte row (chunk c at c ^ ((c >> 3) & 7)), so that lane-major 16-byte
+// reads (lane l: entries 16 l ..) are free of bank conflicts.
+__device__ __forceinline__ long long sm_chunk(long long c) { return c ^ ((c >> 3) & 7); }
+template <int kPer>
+__device__ __forceinline__ long long sm_word(long long e) {
+  return sm_chunk(e / kPer) * kPer + e % kPer;
+}
+// count_below over the 512 staged prefixes of segment s (swizzled).
+__device__ __forceinline__ int count_below_sw(const unsigned long long* P, long long s, unsigned long long X) {
+  const long long base = s * kSeg;
+  int pos = 0;
+#pragma unroll
+  for (int step = kSeg / 2; step > 0; step >>= 1) pos += P[sm_word<2>(base + pos + step - 1)] < X ? step : 0;
+  return pos + (P[sm_word<2>(base + pos)] < X ? 1 : 0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w, long long M, long long N,
+                                                         unsigned long long seed, unsigned long long inst,
+                                                         int* __restrict__ out, int* status, int scheme,
+                                                         const LogTab* __restrict__ tab) {
+  using Tr = FixedTraits<T>;
+  using Bits = typename Tr::Bits;
+  constexpr bool F32 = sizeof(T) == 4;
+  constexpr int kWarps = kSmThreads / 32;
+  constexpr int kPer = 16 / (int)sizeof(T);  // weights per 16-byte chunk
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallSmem<T>& sm = *reinterpret_cast<SmallSmem<T>*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  GBR_BSTAMP(true, 7);
+  Bits* ws = F32 ? reinterpret_cast<Bits*>(sm.w32) : reinterpret_cast<Bits*>(sm.P);  // staged weights
+
+  // the weights: 16-byte asynchronous copies by warps 0-14 (warp 15 computes
+  // 1 / Z_{N+1} while they take the segments), in flight during the draws
+  constexpr int kSegThreads = kSmThreads - 32;
+  const bool vec = (reinterpret_cast<uintptr_t>(w) & 15) == 0;
+  const long long nchunk = vec ? M * (long long)sizeof(T) / 16 : 0;
+  if (tid < kSegThreads) {
+    for (long long q = tid; q < nchunk; q += kSegThreads)
+      cp_async16(reinterpret_cast<char*>(ws) + 16 * sm_chunk(q), reinterpret_cast<const char*>(w) + 16 * q);
+    cp_async_commit();
+  }
+  for (int i = tid; i < 129; i += kSmThreads) {
+    sm.tab.nlogc[i] = tab->nlogc[i];
+    sm.tab.invc[i] = tab->invc[i];
+  }
+  __syncthreads();
+  GBR_BSTAMP(true, 0);
+
+  // ---- Algorithm 1: all N + 1 spacings in one tile, exact prefixes Z_i ------
+  // Multinomial draws with N + 1 <= 1024 take two per thread (one Philox
+  // block serves two threads), else four (one block per thread).
+  const long long ndraw = N + 1;
+  {
+    const int dpt = (scheme == kSchemeMultinomial && ndraw <= 2 * kSmThreads) ? 2 : 4;
+    const long long k0 = (long long)dpt * tid;
+    uint64_t wd[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+    if (k0 < ndraw) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
+    u128 f[4];
+    if (dpt == 2) {
+      const int o = (int)(k0 & 3);  // 0 or 2
+      f[0] = k0 < ndraw ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
+      f[1] = k0 + 1 < ndraw ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
+      f[2] = f[3] = u128{0ULL, 0ULL};
+    } else {
+      block_spacings<F32>(scheme, k0, ndraw, seed, inst, wd, &sm.tab, f);
+    }
+    u128 run = {0ULL, 0ULL}, inc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      run = u128_add(run, f[q]);
+      inc[q] = run;
+    }
+    // the block scan; wsum is not used again, so one barrier suffices
+    const u128 incl = warp_incl_scan_v(run, lane);
+    if (lane == 31) sm.wsum[warp] = incl;
+    __syncthreads();
+    u128 off = {0ULL, 0ULL}, tot = {0ULL, 0ULL};
+#pragma unroll
+    for (int j = 0; j < kWarps; ++j) {
+      const u128 t = sm.wsum[j];
+      if (j < warp) off = u128_add(off, t);
+      tot = u128_add(tot, t);
+    }
+    off = u128_add(off, u128_sub(incl, run));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < dpt && k0 + q < N) sm.key[k0 + q] = u128_add(off, inc[q]);
+    // 1 / Z_{N+1} on warp 15 from here on, while warps 0-14 take the segments
+    if (tid == kSegThreads) sm.invZ = recip_total(tot);
+  }
+  GBR_BSTAMP(true, 1);
+  const int nseg = (int)((M + kSeg - 1) / kSeg);
+  if (warp < kWarps - 1) {
+    cp_async_wait_all();
+    // what the 16-byte copies left (an unaligned start, a ragged end), and
+    // +0 up to the end of the last segment
+    for (long long e = nchunk * kPer + tid; e < (long long)nseg * kSeg; e += kSegThreads) {
+      Bits v = (Bits)0;
+      if (e < M) {
+        if (F32) v = (Bits)__ldg(reinterpret_cast<const unsigned*>(w + e));
+        else v = (Bits)__ldg(reinterpret_cast<const unsigned long long*>(w + e));
+      }
+      ws[sm_word<kPer>(e)] = v;
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(kSegThreads) : "memory");  // warps 0-14 only
+  }
+  GBR_BSTAMP(true, 2);
+
+  // ---- segments (warps 0-14): exact sums and prefixes -----------------------
+  {
+    int em = 0;
+    if (warp < kWarps - 1) {
+#pragma unroll 1
+      for (int s = warp; s < nseg; s += kWarps - 1) {
+        Bits b[kSegV];  // lane-major: elements 16 lane .. 16 lane + 15
+        const long long c0 = ((long long)s * kSeg + lane * kSegV) / kPer;
+#pragma unroll
+        for (int j = 0; j < kSegV / kPer; ++j) {
+          const uint4 v = *reinterpret_cast<const uint4*>(ws + sm_chunk(c0 + j) * kPer);
+          if (F32) {
+            b[4 * j] = (Bits)v.x;
+            b[4 * j + 1] = (Bits)v.y;
+            b[4 * j + 2] = (Bits)v.z;
+            b[4 * j + 3] = (Bits)v.w;
+          } else {
+            b[2 * j] = (Bits)(((unsigned long long)v.y << 32) | v.x);
+            b[2 * j + 1] = (Bits)(((unsigned long long)v.w << 32) | v.z);
+          }
+        }
+        uint64_t F;
+        uint32_t E;
+        seg_sum_bits<T>(b, lane, status, F, E);
+        uint64_t pref[kSegV];
+        seg_prefixes<T>(b, E, lane, pref);
+        // the prefixes replace the segment's weights (each lane its own entries)
+        const long long p0 = ((long long)s * kSeg + lane * kSegV) / 2;
+#pragma unroll
+        for (int j = 0; j < kSegV / 2; ++j)
+          *reinterpret_cast<ulonglong2*>(sm.P + sm_chunk(p0 + j) * 2) = make_ulonglong2(pref[2 * j], pref[2 * j + 1]);
+        if (lane == 0) {
+          sm.F[s] = F;
+          sm.E[s] = (int)E;
+        }
+        em = max(em, (int)E);
+      }
+    }
+    if (lane == 0) sm.emax_w[warp] = em;
+  }
+  __syncthreads();
+  GBR_BSTAMP(true, 3);
+  int Emax = 0;
+#pragma unroll
+  for (int i = 0; i < kWarps; ++i) Emax = max(Emax, sm.emax_w[i]);
+  const long long ge = (long long)Emax - Tr::kBias - Tr::kShift - kGridHead;  // grid exponent
+
+  // ---- grid prefixes (one warp) and c = S / Z_{N+1} --------------------------
+  static_assert(SmallSmem<T>::kMaxSeg <= 32, "one segment a lane");
+  if (warp == 0) {
+    const u128 v = lane < nseg ? grid_value(sm.F[lane], sm.E[lane], Emax) : u128{0ULL, 0ULL};
+    const u128 incl = warp_incl_scan_v(v, lane);
+    if (lane < nseg) sm.pre[lane] = u128_sub(incl, v);
+    if (lane == 31) {
+      sm.pre[nseg] = incl;  // S
+      sm.c = u128_is_zero(incl) ? lb_zero<xf>() : xf_mul(xf_make(incl.hi, incl.lo, 0), sm.invZ);
+    }
+  }
+  __syncthreads();
+  GBR_BSTAMP(true, 4);
+  if (u128_is_zero(sm.pre[nseg])) {
+    if (tid == 0) raise_status(status, ST_EZEROSUM);
+    for (long long i = tid; i < N; i += kSmThreads) out[i] = 0;
+    return;
+  }
+  const xf c = sm.c;
+  for (long long i = tid; i < N; i += kSmThreads) sm.key[i] = map_key(c, sm.key[i]);
+  __syncthreads();
+  GBR_BSTAMP(true, 5);
+
+  // ---- the map (Eq. 2 by Algorithm 5's split argument, one CTA) --------------
+  const long long i0 = N * warp / kWarps, i1 = N * (warp + 1) / kWarps;
+#pragma unroll 1
+  for (long long r0 = i0; r0 < i1; r0 += 32) {
+    const long long i = r0 + lane;
+    const bool valid = i < i1;
+    const u128 key = valid ? sm.key[i] : u128{0ULL, 0ULL};
+    // the segment: how many of the prefixes P_1 .. P_{nseg-1} lie below the key
+    int s_me = 0;
+    if (valid) {
+      int lo = 1, hi = nseg;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (u128_lt(sm.pre[mid], key)) lo = mid + 1;
+        else hi = mid;
+      }
+      s_me = lo - 1;
+    }
+    const u128 Ps = sm.pre[s_me];
+    const uint32_t E = (uint32_t)sm.E[s_me];
+    const unsigned long long Fs = sm.F[s_me];
+    const int sh = (int)E - Emax + kGridHead;
+    const long long rem_len = M - (long long)s_me * kSeg;
+    const int len = (int)(rem_len < kSeg ? rem_len : kSeg);
+    const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
+    const unsigned long long Kq = ceil_units(rem, sh, Fs);
+    int cnt = valid ? count_below_sw(sm.P, s_me, Kq) : 0;
+    if (!F32) {
+      // a head segment: the prefix before it is too small for the segment
+      // grid to decide every key exactly; the ambiguous keys are decided by
+      // exact per-element sums (as on every other path)
+      bool amb = false;
+      if (valid) {
+        const xf Px = xf_make(Ps.hi, Ps.lo, 0);
+        const xf rx = xf_make(rem.hi, rem.lo, 0);
+        if ((xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50) && (xf_zero(rx) || rx.e + kXfTop < (long long)sh + 50)) {
+          if (Kq >= Fs) amb = true;
+          else if ((long long)Kq <= len) amb = cnt > 0;
+          else amb = count_below_sw(sm.P, s_me, Kq - (unsigned long long)len) != cnt;
+        }
+      }
+      unsigned gx = __ballot_sync(0xFFFFFFFFu, amb);
+#pragma unroll 1
+      while (gx) {
+        const int jl = __ffs(gx) - 1;
+        gx &= gx - 1;
+        const u128 rj = shfl_v(rem, jl);
+        const long long sj = __shfl_sync(0xFFFFFFFFu, s_me, jl);
+        const int cj = vec ? head_count<true>(reinterpret_cast<const double*>(w), sj * kSeg, M,
+                                              xf_make(rj.hi, rj.lo, ge), lane)
+                           : head_count<false>(reinterpret_cast<const double*>(w), sj * kSeg, M,
+                                               xf_make(rj.hi, rj.lo, ge), lane);
+        if (lane == jl) cnt = cj;
+      }
+    }
+    if (valid) {
+      const int jj = cnt < len ? cnt : len - 1;
+      long long idx = (long long)s_me * kSeg + jj;
+      if (idx > M - 1) idx = M - 1;
+      out[i] = (int)idx;
+    }
+  }
+#ifdef GBR_PHASE_STAMPS
+  __syncthreads();
+  GBR_BSTAMP(true, 6);
+#endif
+}
+
 template <typename T, int kThreads>
 static cudaError_t batched_t(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
                              unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
@@ -486,6 +764,28 @@ cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, cons
                                    threads, leaf_T, out, queue, status, st, scheme, tab);
   return batched_dispatch<double>(static_cast<const double*>(w), w_off, r_off, order, K, seed, inst_base, M0, N0,
                                   threads, leaf_T, out, queue, status, st, scheme, tab);
+}
+
+size_t small_smem_bytes(bool f32) { return f32 ? sizeof(SmallSmem<float>) : sizeof(SmallSmem<double>); }
+
+cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,
+                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab) {
+  if (N <= 0 || M <= 0) return cudaSuccess;
+  if (N > kSmallMaxN || M > kSmallMaxM) return cudaErrorInvalidValue;
+  const size_t smem = small_smem_bytes(f32);
+  cudaError_t e;
+  if (f32) {
+    e = cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_small<float><<<1, kSmThreads, smem, st>>>(static_cast<const float*>(w), M, N, seed, inst, out, status, scheme,
+                                                 tab);
+  } else {
+    e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_small<double><<<1, kSmThreads, smem, st>>>(static_cast<const double*>(w), M, N, seed, inst, out, status,
+                                                  scheme, tab);
+  }
+  return cudaGetLastError();
 }
 
 // ---- work order: instances by M_k descending (ties by index) ----------------

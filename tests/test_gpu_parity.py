@@ -389,6 +389,71 @@ def test_fused_equals_multikernel(g, h, prec, M, N, path):
     assert np.array_equal(host(a), host(b))
 
 
+SMALL_CASES = [(1, 1), (3, 2047), (511, 7), (512, 512), (4096, 1024), (5000, 2047), (12_287, 300), ("max", 2047)]
+
+
+@pytest.mark.parametrize("scheme", ["multinomial", "stratified", "systematic"])
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("M,N", SMALL_CASES)
+def test_small_smem_equals_other_forms(g, h, prec, M, N, aligned, scheme):
+    """The one-CTA form with the weights staged in shared memory (at most
+    12,288 weights, 2047 samples) against the cooperative launch and the
+    multi-kernel path, index for index, for 16-byte aligned weights (copied
+    asynchronously) and unaligned ones (plain loads), under every scheme."""
+    if M == "max":
+        M = 12_288
+    w = workloads.weights_lognormal(M + 1, 2.0, seed=M + N)
+    p = g.RS_F64 if prec == "f64" else g.RS_F32_COMP
+    if prec == "f32":
+        w = w.astype(np.float32)
+    base = dev(w)
+    wd = base[:M] if aligned else base[1:]  # one element in: 4- or 8-byte aligned only
+    sc = {"multinomial": g.RS_SCHEME_MULTINOMIAL, "stratified": g.RS_SCHEME_STRATIFIED,
+          "systematic": g.RS_SCHEME_SYSTEMATIC}[scheme]
+    outs = []
+    for flags in (0, 4, 2):
+        r = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+        g.rs_resample_w(h.h, wd, M, N, 21, 5, r, None, g.opts(prec=p, debug_flags=flags, scheme=sc))
+        outs.append(host(r))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[2])
+    assert outs[0].min() >= 0 and outs[0].max() < M
+
+
+@pytest.mark.parametrize("kind", workloads.ADVERSARIAL)
+@pytest.mark.parametrize("M,N", [(12_288, 2047), (1500, 700)])
+def test_small_smem_adversarial(g, h, kind, M, N):
+    """Adversarial binary64 weights (ties, zero runs, head segments, a spike)
+    on the shared-memory one-CTA form against the multi-kernel path."""
+    w = workloads.adversarial_weights(kind, M, seed=6)
+    wd = dev(w)
+    a = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    b = torch.full((N,), -2, dtype=torch.int32, device="cuda")
+    g.rs_resample_w(h.h, wd, M, N, 8, 1, a)
+    g.rs_resample_w(h.h, wd, M, N, 8, 1, b, None, g.opts(debug_flags=2))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(host(a), host(b))
+
+
+def test_small_smem_is_taken(g, h):
+    """The small workload's shape (M = 4096, N = 1024) runs on the
+    shared-memory one-CTA form; 20,000 binary64 weights on the other one."""
+    out = torch.empty(1024, dtype=torch.int32, device="cuda")
+    wd = dev(workloads.weights_lognormal(20_000, 2.0, seed=2))
+    g.rs_trace_enable(h.h, True)
+    try:
+        g.rs_resample_w(h.h, wd, 4096, 1024, 1, 0, out)
+        g.rs_resample_w(h.h, wd, 20_000, 1024, 1, 0, out)
+        g.rs_trace_collect(h.h)
+        rep = g.rs_trace_report(h.h)
+    finally:
+        g.rs_trace_enable(h.h, False)
+        g.rs_trace_reset(h.h)
+    assert h.status() == g.RS_OK
+    assert rep["small_smem"][0] == 1 and rep["single_cta"][0] == 1, rep
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("which", ["all_few", "mixed", "all_many"])
 def test_fused_draw_split_modes(g, h, prec, which):
