@@ -844,6 +844,15 @@ rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uin
   if (!W || !aligned(W, 8)) return fail(h, RS_EINVAL, "W must be a non-NULL 8-byte aligned pointer");
   if (!out_idx || !aligned(out_idx, 4)) return fail(h, RS_EINVAL, "out_idx must be a non-NULL pointer");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (M <= kSmallMaxM && N <= kSmallMaxN && !(o.debug & 5)) {
+    // a small instance: the uniforms and the map on one CTA, W in shared
+    // memory; the DaC leaves are one per thread unless opts->leaf_L is set
+    const int L = o.leaf_L > 0 ? o.leaf_L : (int)((N + kSmallThreadsW - 1) / kSmallThreadsW);
+    RS_TRACE(h, "small_W", st);
+    RS_CK(h, launch_small_W(o.prec == RS_F32_COMP, o.algo, W, M, N, seed, instance, L, out_idx, st, o.scheme,
+                            static_cast<const LogTab*>(h->logtab)));
+    return RS_OK;
+  }
   const Plan p = make_plan(0, N, false, true, true);
   if ((s = ensure_ws(h, p.bytes))) return s;
   if (N <= kUSmallMaxN && !(o.debug & 5)) {  // the sorted uniforms by one CTA, one launch

@@ -245,6 +245,193 @@ __global__ void __launch_bounds__(256) k_map_linear(const double* __restrict__ W
   }
 }
 
+// ---------------------------------------------------------------------------
+// The sampling steps of a small instance on one CTA (M <= 12,288, N <= 2047):
+// W travels to shared memory while the draws are made; then 1 / Z_{N+1} (warp
+// 15), U_i exactly as the one-CTA uniform kernel forms it, and the map named
+// by kAlgo over W in shared memory:
+//   kMapDac     Algorithm 5: leaves of L samples; each leaf's last sample is
+//               located in W[0, M-1], its first in [0, r_last] (the split
+//               argument), and the samples between walk forward from there;
+//   kMapBinary  Algorithm 3: one lower-bound search of W per sample;
+//   kMapLinear  Algorithm 4: thread t owns W[M t / 512, M (t+1) / 512) and the
+//               samples whose answers fall there, found by one search of U,
+//               and merge-walks them.
+// Comparisons are exact (total-order integer keys), so all three equal the
+// multi-launch maps bit for bit.
+enum : int { kMapDac = 0, kMapBinary = 1, kMapLinear = 2 };
+constexpr int kSwThreads = kSmallThreadsW;
+struct SmallWSmem {
+  long long Wk[kSmallMaxM];  // W's bits, then their total-order keys
+  long long Uk[kSmallMaxN];  // the keys of U
+  u128 wsum[kSwThreads / 32];
+  xf r;
+  LogTab tab;
+};
+__device__ __forceinline__ long long lower_bound_sm(const long long* Wk, long long a, long long b, long long key) {
+  while (a < b) {  // smallest m in [a, b] with Wk[m] >= key, else b
+    const long long m = (a + b) >> 1;
+    if (Wk[m] < key) a = m + 1;
+    else b = m;
+  }
+  return b;
+}
+
+template <bool F32, int kAlgo>
+__global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restrict__ W, long long M, long long N,
+                                                           unsigned long long seed, unsigned long long inst, int L,
+                                                           int* __restrict__ out, int scheme,
+                                                           const LogTab* __restrict__ tab) {
+  constexpr int kWarps = kSwThreads / 32;
+  constexpr int kCopyThreads = kSwThreads - 32;  // warp 15 computes 1 / Z_{N+1} meanwhile
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallWSmem& sm = *reinterpret_cast<SmallWSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool vec = (reinterpret_cast<uintptr_t>(W) & 15) == 0;
+  const long long nchunk = vec ? M / 2 : 0;  // 16-byte chunks
+  if (tid < kCopyThreads) {
+    for (long long q = tid; q < nchunk; q += kCopyThreads)
+      cp_async16(sm.Wk + 2 * q, reinterpret_cast<const char*>(W) + 16 * q);
+    cp_async_commit();
+  }
+  for (int i = tid; i < 129; i += kSwThreads) {
+    sm.tab.nlogc[i] = tab->nlogc[i];
+    sm.tab.invc[i] = tab->invc[i];
+  }
+  __syncthreads();
+
+  // ---- Algorithm 1, exactly as the one-CTA uniform kernel ------------------
+  const long long ndraw = N + 1;
+  const int dpt = (scheme == kSchemeMultinomial && ndraw <= 2 * kSwThreads) ? 2 : 4;
+  const long long k0 = (long long)dpt * tid;
+  u128 z[4];
+  {
+    uint64_t wd[4] = {0ULL, 0ULL, 0ULL, 0ULL};
+    if (k0 < ndraw) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
+    u128 f[4];
+    if (dpt == 2) {
+      const int o = (int)(k0 & 3);
+      f[0] = k0 < ndraw ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
+      f[1] = k0 + 1 < ndraw ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
+      f[2] = f[3] = u128{0ULL, 0ULL};
+    } else {
+      block_spacings<F32>(scheme, k0, ndraw, seed, inst, wd, &sm.tab, f);
+    }
+    u128 run = {0ULL, 0ULL};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      run = u128_add(run, f[q]);
+      z[q] = run;
+    }
+    const u128 incl = warp_incl_scan_v(run, lane);
+    if (lane == 31) sm.wsum[warp] = incl;
+    __syncthreads();
+    u128 off = {0ULL, 0ULL}, tot = {0ULL, 0ULL};
+#pragma unroll
+    for (int j = 0; j < kWarps; ++j) {
+      const u128 t = sm.wsum[j];
+      if (j < warp) off = u128_add(off, t);
+      tot = u128_add(tot, t);
+    }
+    off = u128_add(off, u128_sub(incl, run));
+#pragma unroll
+    for (int q = 0; q < 4; ++q) z[q] = u128_add(off, z[q]);  // Z_{k0+q+1}
+    if (tid == kCopyThreads) sm.r = u128_is_zero(tot) ? lb_zero<xf>() : recip_total(tot);
+  }
+  if (tid < kCopyThreads) {
+    cp_async_wait_all();
+    for (long long e = 2 * nchunk + tid; e < M; e += kCopyThreads)
+      sm.Wk[e] = __ldg(reinterpret_cast<const long long*>(W + e));
+    asm volatile("bar.sync 1, %0;" ::"n"(kCopyThreads) : "memory");
+    for (long long e = tid; e < M; e += kCopyThreads) sm.Wk[e] = ord_key_bits(sm.Wk[e]);
+  }
+  __syncthreads();
+  {
+    const xf r = sm.r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < dpt && k0 + q < N) {
+        long long ub = (long long)xf_to_f64_bits(xf_mul_u128(r, z[q]));
+        if (ub > 0x3FF0000000000000LL) ub = 0x3FF0000000000000LL;
+        sm.Uk[k0 + q] = ord_key_bits(ub);
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- the map ----------------------------------------------------------------
+  const long long* Wk = sm.Wk;
+  const long long* Uk = sm.Uk;
+  if (kAlgo == kMapBinary) {
+    for (long long i = tid; i < N; i += kSwThreads) out[i] = (int)lower_bound_sm(Wk, 0, M - 1, Uk[i]);
+  } else if (kAlgo == kMapLinear) {
+    const long long a = M * tid / kSwThreads, b = M * (tid + 1) / kSwThreads;
+    if (a < b) {
+      // the slice's samples: W[a-1] < U_i <= W[b-1] (the last slice: all above W[a-1])
+      long long i = 0;
+      if (a > 0) {
+        long long lo = 0, hi = N;
+        while (lo < hi) {
+          const long long m = (lo + hi) >> 1;
+          if (Uk[m] <= Wk[a - 1]) lo = m + 1;
+          else hi = m;
+        }
+        i = lo;
+      }
+      const bool last = b == M;
+      long long j = a;
+      for (; i < N; ++i) {
+        const long long k = Uk[i];
+        if (!last && k > Wk[b - 1]) break;
+        while (j < M - 1 && Wk[j] < k) ++j;
+        out[i] = (int)j;
+      }
+    }
+  } else {
+    const long long nleaf = (N + L - 1) / L;
+    for (long long leaf = tid; leaf < nleaf; leaf += kSwThreads) {
+      const long long a = leaf * (long long)L;
+      const long long b = (a + L < N ? a + L : N) - 1;
+      const long long rb = lower_bound_sm(Wk, 0, M - 1, Uk[b]);
+      long long j = lower_bound_sm(Wk, 0, rb, Uk[a]);
+      out[a] = (int)j;
+      for (long long i = a + 1; i <= b; ++i) {
+        const long long k = Uk[i];
+        while (j < rb && Wk[j] < k) ++j;
+        out[i] = (int)j;
+      }
+    }
+  }
+}
+
+template <bool F32>
+static cudaError_t small_W_t(int algo, const double* W, long long M, long long N, unsigned long long seed,
+                             unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab) {
+  const size_t smem = sizeof(SmallWSmem);
+  cudaError_t e;
+#define GBR_SMALL_W(A)                                                                                         \
+  e = cudaFuncSetAttribute(k_small_W<F32, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+  if (e != cudaSuccess) return e;                                                                              \
+  k_small_W<F32, A><<<1, kSwThreads, smem, st>>>(W, M, N, seed, inst, L, out, scheme, tab);
+  if (algo == kMapBinary) {
+    GBR_SMALL_W(kMapBinary)
+  } else if (algo == kMapLinear) {
+    GBR_SMALL_W(kMapLinear)
+  } else {
+    GBR_SMALL_W(kMapDac)
+  }
+#undef GBR_SMALL_W
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_W(bool f32, int algo, const double* W, long long M, long long N, unsigned long long seed,
+                           unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab) {
+  if (N <= 0 || M <= 0) return cudaSuccess;
+  if (N > kSmallMaxN || M > kSmallMaxM || L < 1) return cudaErrorInvalidValue;
+  return f32 ? small_W_t<true>(algo, W, M, N, seed, inst, L, out, st, scheme, tab)
+             : small_W_t<false>(algo, W, M, N, seed, inst, L, out, st, scheme, tab);
+}
+
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   long long blocks = (N + 255) / 256;

@@ -274,6 +274,51 @@ def test_resample_W_map_only(g, h, algo):
     assert_boundary_only(host(out), r_ref, W, U_ref, rel=REL_F64)
 
 
+SMALL_W_CASES = [(1, 1), (7, 2047), (600, 3), (4096, 1024), (5000, 300), (12_288, 2047)]
+
+
+@pytest.mark.parametrize("scheme", ["multinomial", "stratified", "systematic"])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("algo", ["dac", "binary", "linear"])
+@pytest.mark.parametrize("M,N", SMALL_W_CASES)
+def test_resample_W_one_cta_equals_multilaunch(g, h, M, N, algo, prec, scheme):
+    """rs_resample_W on one CTA (W in shared memory, at most 12,288 weights
+    and 2047 samples) against the multi-launch form (debug bit 2), index for
+    index, for the three maps, both draw precisions, every scheme, and an
+    8-byte (not 16-byte) aligned W; ties with W and an all-zero head."""
+    w = workloads.adversarial_weights("zeros_runs", M + 1, seed=M + N)
+    W, _ = oracle.cumulative(w)
+    a = {"dac": g.RS_MAP_DAC, "binary": g.RS_MAP_BINARY, "linear": g.RS_MAP_LINEAR}[algo]
+    sc = {"multinomial": g.RS_SCHEME_MULTINOMIAL, "stratified": g.RS_SCHEME_STRATIFIED,
+          "systematic": g.RS_SCHEME_SYSTEMATIC}[scheme]
+    p = g.RS_F64 if prec == "f64" else g.RS_F32_COMP
+    Wd = dev(W)
+    outs = []
+    for Wv in (Wd[:M], Wd[1:]):  # 16-byte aligned, then 8-byte aligned
+        for flags in (0, 4):
+            r = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+            g.rs_resample_W(h.h, Wv, M, N, 13, 2, r, g.opts(algo=a, prec=p, scheme=sc, debug_flags=flags))
+            outs.append(host(r))
+    assert h.status() == g.RS_OK
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[2], outs[3])
+    assert outs[0].min() >= 0 and outs[0].max() < M
+
+
+@pytest.mark.parametrize("L", [1, 4, 64, 1024])
+def test_resample_W_one_cta_leaf_sizes(g, h, L):
+    """The one-CTA divide and conquer with explicit leaf sizes (one sample a
+    leaf up to one leaf for all) against the oracle's walk on the same U."""
+    M, N = 4096, 1024
+    w = workloads.weights_lognormal(M, 2.0, seed=L)
+    W, _ = oracle.cumulative(w)
+    U_ref = oracle.sorted_uniform(N, 8, 0)
+    r_ref = oracle.inverse_cdf_walk(W, U_ref)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    g.rs_resample_W(h.h, dev(W), M, N, 8, 0, out, g.opts(algo=g.RS_MAP_DAC, leaf_L=L))
+    assert h.status() == g.RS_OK
+    assert_boundary_only(host(out), r_ref, W, U_ref, rel=REL_F64)
+
+
 def test_resample_batched_matches_instances(g, h):
     w, woff, roff = workloads.weights_batched(K=24, seed=5, nmin=8, nmax=300, pmax=9)
     K = 24
