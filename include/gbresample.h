@@ -105,7 +105,9 @@ typedef struct {
                           the multi-kernel path instead of the single cooperative
                           launch (identical results; for comparison).  Bit 2: the
                           one-CTA paths of small instances (rs_resample_w up to
-                          32,768 weights and 2,048 samples, both forms; the sorted uniforms of
+                          32,768 weights and 2,048 samples, both forms;
+                          rs_resample_W up to 12,288 weights and 2,047
+                          samples; the sorted uniforms of
                           rs_sorted_uniform and rs_resample_W up to 2,047
                           samples) are not taken (identical results; for
                           comparison).  Bit 0 also keeps the uniforms on the
@@ -145,7 +147,11 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
  * "sampling steps", W excluded).
  *  W       [M] binary64 cumulative weights, non-decreasing, W_M = 1 expected
  *          (not checked: a U above W_M is clamped to M-1).
- *  out_idx [N] int32, written.  opts->algo selects the map. */
+ *  out_idx [N] int32, written.  opts->algo selects the map.
+ * Launch forms, all giving identical indices: M <= 12,288 and N <= 2,047 run
+ * on one CTA (W staged in shared memory, the DaC leaves one per thread unless
+ * opts->leaf_L is set); otherwise the sorted uniforms (one CTA up to 2,047
+ * samples, else a look-back scan) and then the map kernel. */
 rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
                         int32_t* out_idx, const rs_opts* opts, void* stream);
 
