@@ -92,9 +92,10 @@ typedef struct {
   int32_t prec;        /* rs_precision (default RS_F64) */
   int32_t leaf_L;      /* DaC: samples per leaf (power of two 1..1024; 0 = choose from M/N).
                           rs_resample_batched: the leaf threshold - a segment holding at
-                          most leaf_L samples is resolved by a warp-wide count over its
-                          512 prefixes (linear walk), a fuller one by per-sample binary
-                          search (0 = the autotuned or default value) */
+                          most leaf_L samples is resolved per sample from its 32 lane
+                          prefixes and the one 16-weight block holding the target, a
+                          fuller one from all 512 prefixes by per-sample binary search
+                          (0 = the autotuned or default value) */
   int32_t stage_max;   /* DaC: largest W range a leaf stages in shared memory (0 = default 512) */
   int32_t spin_limit;  /* bounded-wait iterations before RS_ETIMEOUT (0 = default) */
   int32_t debug_flags; /* test hook, 0 in normal use.  Bit 0: the first tile of every
@@ -274,14 +275,14 @@ rs_status rs_gather(rs_handle* h, const void* x, int64_t M, int64_t row_bytes, c
  * opts->leaf_L select the CTA size and the leaf threshold; 0 takes the values
  * rs_autotune_batched stored in the handle (or rs_tuning_load read) for the
  * batch's precision and nearest M/N bucket, or
- * defaults (256, 4). */
+ * defaults (256, 16). */
 rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off, const int64_t* r_off, int32_t K,
                               const int64_t* h_w_off, const int64_t* h_r_off, uint64_t seed, int32_t* out_idx,
                               const rs_opts* opts, void* stream);
 
 /* Autotuner of rs_resample_batched: runs the call (same arguments, which must
  * be valid; outputs are written) for each candidate CTA size {128, 256, 512}
- * and leaf threshold {1, 4, 32}, times each with CUDA events on `stream`
+ * and leaf threshold {4, 16, 64}, times each with CUDA events on `stream`
  * (one warm-up, three timed runs), keeps the fastest in the handle for later
  * calls with zero tile_threads / leaf_L, and writes it to *best (may be NULL):
  * best->tile_threads, best->leaf_L, best->prec.  Synchronises the stream; call

@@ -76,6 +76,9 @@ constexpr int kStageCap = 512;  // shared-memory staging capacity of the DaC lea
 // CTA: the persistent kernel's single-instance form, one launch, no
 // inter-CTA exchange.
 constexpr long long kSmallM = 1LL << 15;
+// Default leaf threshold of the persistent kernel (segments with at most
+// this many samples are decided from lane prefixes and one weight block).
+constexpr int kBatchedLeafDefault = 16;
 
 rs_status fail(rs_handle* h, rs_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -769,9 +772,13 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
   }
   if (N > 0 && !W_out && !(o.debug & 6) && M <= kSmallM && N <= kBMaxN) {
     // a small instance: the whole path on one CTA
+    Layout L;
+    const size_t o_lp = L.take(batched_scratch_bytes(f32, 256, 1, false));
+    if ((s = ensure_ws(h, L.off))) return s;
     RS_TRACE(h, "single_cta", st);
-    RS_CK(h, launch_batched(f32, w, nullptr, nullptr, nullptr, 1, seed, instance, M, N, 256, 4, out_idx, nullptr,
-                            h->status, st, o.scheme, static_cast<const LogTab*>(h->logtab)));
+    RS_CK(h, launch_batched(f32, w, nullptr, nullptr, nullptr, 1, seed, instance, M, N, 256, kBatchedLeafDefault,
+                            out_idx, nullptr, h->status, st, o.scheme, static_cast<const LogTab*>(h->logtab),
+                            at<unsigned long long>(h, o_lp)));
     return RS_OK;
   }
   const Plan p = make_plan(M, N, true, N > 0, false, W_out != nullptr);
@@ -984,13 +991,14 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
     if ((s = rs_resample_w(h, wk, Mk, Nk, seed, (uint64_t)k, out_idx + ro[k], nullptr, &one, stream))) return s;
   }
   if (per_instance) return RS_OK;
+  const rs_tune_entry* tb = find_tune(h, "batched", f32, mn_bucket(wo[K], ro[K]));
+  const int threads = o.threads ? o.threads : (tb ? tb->threads : 256);
+  const int leaf = o.leaf_L ? o.leaf_L : (tb ? tb->leaf : kBatchedLeafDefault);
   Layout L;
   const size_t o_queue = L.take(256);
   const size_t o_order = L.take((size_t)K * sizeof(int));
+  const size_t o_lp = L.take(batched_scratch_bytes(f32, threads, K, true));
   if ((s = ensure_ws(h, L.off))) return s;
-  const rs_tune_entry* tb = find_tune(h, "batched", f32, mn_bucket(wo[K], ro[K]));
-  const int threads = o.threads ? o.threads : (tb ? tb->threads : 256);
-  const int leaf = o.leaf_L ? o.leaf_L : (tb ? tb->leaf : 4);
   {
     RS_TRACE(h, "batched_order", st);
     RS_CK(h, cudaMemsetAsync(at<unsigned>(h, o_queue), 0, 256, st));
@@ -1001,7 +1009,7 @@ rs_status rs_resample_batched(rs_handle* h, const void* w, const int64_t* w_off,
     RS_CK(h, launch_batched(f32, w, reinterpret_cast<const long long*>(w_off),
                             reinterpret_cast<const long long*>(r_off), at<int>(h, o_order), K, seed, 0ULL, 0, 0,
                             threads, leaf, out_idx, at<unsigned>(h, o_queue), h->status, st, o.scheme,
-                            static_cast<const LogTab*>(h->logtab)));
+                            static_cast<const LogTab*>(h->logtab), at<unsigned long long>(h, o_lp)));
   }
   return RS_OK;
 }
@@ -1066,7 +1074,7 @@ rs_status rs_autotune_batched(rs_handle* h, const void* w, const int64_t* w_off,
   if ((s = read_opts(h, opts, &o, RS_F32_COMP))) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   static const int kThreadsC[3] = {128, 256, 512};
-  static const int kLeafC[3] = {1, 4, 32};
+  static const int kLeafC[3] = {4, 16, 64};
   rs_opts c;
   memset(&c, 0, sizeof(c));
   c.prec = o.prec;

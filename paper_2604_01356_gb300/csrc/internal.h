@@ -157,10 +157,15 @@ cudaError_t launch_batched_order(const long long* w_off, int K, int* order, cuda
 // instance (M0, N0); queue == nullptr: CTA b takes instance b (launch K
 // CTAs); order == nullptr: identity order.  Instance k draws from the Philox
 // stream (seed, inst_base + k).
+// leaf_T: segments holding at most this many samples are decided from their
+// 32 lane prefixes and one 16-weight block per sample; denser ones from all
+// their prefixes.  lpref: scratch of batched_scratch_bytes(f32, threads, K,
+// queue != nullptr) bytes (the lane prefixes, kBMaxSeg x 32 per CTA).
+size_t batched_scratch_bytes(bool f32, int threads, int K, bool queue);
 cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, const long long* r_off, const int* order,
                            int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
                            int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
-                           const LogTab* tab);
+                           const LogTab* tab, unsigned long long* lpref);
 // --- one-CTA whole path of a small instance, weights staged in shared memory
 // (512 threads; N + 1 <= 2048 draws in one tile; at most kSmallMaxM
 // weights).  Indices equal those of every other form of rs_resample_w.

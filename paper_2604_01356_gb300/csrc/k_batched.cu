@@ -88,6 +88,59 @@ __device__ __forceinline__ u128 block_excl_scan(u128 v, u128* wsum, u128& total)
   return u128_add(off, u128_sub(incl, v));
 }
 
+// The striped layout (load_seg_striped) gives each lane runs of kRun
+// consecutive weights: run j of lane l starts at element 32 kRun j + kRun l.
+// From the lanes' run sums g (seg_sum_bits_groups), lane L returns the
+// inclusive prefix of block L (elements 16 L .. 16 L + 15): the runs of one
+// block sit in 16 / kRun neighbouring lanes of one row.
+template <int kRun>
+__device__ __forceinline__ unsigned long long striped_block_prefix(uint64_t (&g)[kSegV / kRun], int lane) {
+  constexpr int kLanesPerBlock = 16 / kRun;
+  constexpr int kBlocksPerRow = 32 / kLanesPerBlock;
+  constexpr int kRows = kSegV / kRun;
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+#pragma unroll
+    for (int o = 1; o < kLanesPerBlock; o <<= 1) g[j] += __shfl_xor_sync(0xFFFFFFFFu, g[j], o);
+  }
+  const int src = (lane % kBlocksPerRow) * kLanesPerBlock;
+  uint64_t v = 0;
+#pragma unroll
+  for (int j = 0; j < kRows; ++j) {
+    const uint64_t t = __shfl_sync(0xFFFFFFFFu, g[j], src);
+    if (lane / kBlocksPerRow == j) v = t;
+  }
+  return warp_incl_scan_u64(v, lane);
+}
+
+// Number of a segment's 512 exact prefixes below X, from its 32 inclusive
+// lane prefixes lp (lane l: elements 16 l .. 16 l + 15, in shared memory) and
+// the 16 weights of the one lane block where X is reached: the blocks before
+// it lie entirely below X, those after it entirely at or above, and inside
+// it the prefixes are rebuilt exactly.  Equals count_below over the full
+// prefixes (512 when every prefix is below X).
+template <typename T, bool kVec>
+__device__ __forceinline__ int block_count(const unsigned long long* lp, const T* __restrict__ w, long long base,
+                                           long long M, uint32_t E, unsigned long long X) {
+  int lo = 0, hi = 32;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lp[mid] < X) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo >= 32) return kSeg;
+  typename FixedTraits<T>::Bits b[kSegV];
+  load_seg_blocked<T, kVec>(w, base, M, lo, b);
+  unsigned long long run = lo ? lp[lo - 1] : 0ULL;
+  int c = 0;
+#pragma unroll
+  for (int q = 0; q < kSegV; ++q) {
+    run += FixedTraits<T>::fixed(b[q], E);
+    c += run < X ? 1 : 0;
+  }
+  return lo * kSegV + c;
+}
+
 // Number of the 512 non-decreasing entries p[0..511] below X: nine fixed
 // halving steps and a last compare, no branch.
 __device__ __forceinline__ int count_below(const unsigned long long* p, unsigned long long X) {
@@ -115,12 +168,14 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
                                                       const int* __restrict__ order, int K, unsigned long long seed,
                                                       unsigned long long inst_base, long long M0, long long N0,
                                                       int leaf_T, int* __restrict__ out, unsigned* queue,
-                                                      int* status, int scheme, const LogTab* __restrict__ tab) {
+                                                      int* status, int scheme, const LogTab* __restrict__ tab,
+                                                      unsigned long long* __restrict__ lpref) {
   using Tr = FixedTraits<T>;
   using Bits = typename Tr::Bits;
   constexpr bool F32 = sizeof(T) == 4;
   constexpr int kWarps = kThreads / 32;
   constexpr int kChunk = kThreads * 4;  // draws per block per chunk (4 per thread)
+  constexpr int kRun = 16 / (int)sizeof(T);  // consecutive weights a lane holds in the striped layout
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BatchSmem<kWarps>& sm = *reinterpret_cast<BatchSmem<kWarps>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -158,6 +213,10 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
 
     GBR_BSTAMP(first, 1);
     // ---- A: exact segment sums, two segments in flight per warp --------------
+    // Besides each segment's sum, the inclusive prefixes of its 32 blocks of
+    // 16 consecutive weights (exact, on the segment grid) go to lpb for the
+    // map; the striped (coalesced) loads give them through a few shuffles.
+    unsigned long long* lpb = lpref + (long long)blockIdx.x * kBMaxSeg * 32;
     int em = 0;
     for (int s0 = warp; s0 < nseg; s0 += 2 * kWarps) {
       const int s1 = s0 + kWarps;
@@ -171,14 +230,17 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
       }
       uint64_t F;
       uint32_t E;
-      seg_sum_bits<T>(b0, lane, status, F, E);
+      uint64_t g[kSegV / kRun];
+      seg_sum_bits_groups<T, kRun>(b0, lane, status, F, E, g);
+      lpb[(long long)s0 * 32 + lane] = striped_block_prefix<kRun>(g, lane);
       if (lane == 0) {
         sm.F[s0] = F;
         sm.E[s0] = (int)E;
       }
       em = max(em, (int)E);
       if (s1 < nseg) {
-        seg_sum_bits<T>(b1, lane, status, F, E);
+        seg_sum_bits_groups<T, kRun>(b1, lane, status, F, E, g);
+        lpb[(long long)s1 * 32 + lane] = striped_block_prefix<kRun>(g, lane);
         if (lane == 0) {
           sm.F[s1] = F;
           sm.E[s1] = (int)E;
@@ -273,8 +335,12 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
       unsigned long long* sp = sm.pref[warp];
       Bits bn[kSegV];
       int pf = -1;
+      // the lane prefixes of the next segment travel while one is resolved
+      unsigned long long lp_next = sa < sb ? __ldcg(lpb + (long long)sa * 32 + lane) : 0ULL;
 #pragma unroll 1
       for (int sc = sa; sc < sb && i < Nk; ++sc) {
+        const unsigned long long lp_this = lp_next;
+        if (sc + 1 < sb) lp_next = __ldcg(lpb + (long long)(sc + 1) * 32 + lane);
         const bool last = sc == (int)nseg - 1;
         const u128 Pn = sm.pre[sc + 1];
         // samples [i, ie) fall in segment sc: the first key above P_{sc+1}
@@ -300,21 +366,6 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
           }
         }
         if (ie == i) continue;
-        Bits b[kSegV];
-        if (pf == sc) {
-#pragma unroll
-          for (int q = 0; q < kSegV; ++q) b[q] = bn[q];
-        } else if (vec) {
-          load_seg_blocked<T, true>(wk, (long long)sc * kSeg, Mk, lane, b);
-        } else {
-          load_seg_blocked<T, false>(wk, (long long)sc * kSeg, Mk, lane, b);
-        }
-        pf = -1;
-        if (F32 && sc + 1 < sb) {  // the next segment's weights travel while this one is resolved
-          if (vec) load_seg_blocked<T, true>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
-          else load_seg_blocked<T, false>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
-          pf = sc + 1;
-        }
         const uint32_t E = (uint32_t)sm.E[sc];
         const unsigned long long Fs = sm.F[sc];
         const u128 Ps = sm.pre[sc];
@@ -330,53 +381,82 @@ __global__ void __launch_bounds__(kThreads) k_batched(const T* __restrict__ w, c
           const xf Px = xf_make(Ps.hi, Ps.lo, 0);
           head = xf_zero(Px) || Px.e + kXfTop < (long long)sh + 50;
         }
-        uint64_t pref[kSegV];
-        seg_prefixes<T>(b, E, lane, pref);
         if (ie - i <= leaf_T) {
-          // a few samples: a warp-wide count over the prefixes in registers
-          // (the linear-walk leaf)
+          // few samples (the leaf threshold): each sample is decided from
+          // the segment's 32 exact lane prefixes (phase A) and the 16
+          // weights of the one lane block its target falls in, without
+          // decoding the whole segment
+          __syncwarp();
+          sp[lane] = lp_this;
+          __syncwarp();
 #pragma unroll 1
-          for (long long j = i; j < ie; ++j) {
-            const u128 key = sm.key[j];
-            const u128 rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
-            const unsigned long long Kq = ceil_units(rem, sh, Fs);
+          for (long long j0 = i; j0 < ie; j0 += 32) {
+            const long long j = j0 + lane;
+            const bool mine = j < ie;
+            u128 rem = {0ULL, 0ULL};
+            unsigned long long Kq = 1;
             int cnt = 0;
-#pragma unroll
-            for (int q = 0; q < kSegV; ++q) cnt += pref[q] < Kq ? 1 : 0;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
-            if (head) {  // warp-uniform: every lane holds the same key
-              const xf rx = xf_make(rem.hi, rem.lo, 0);
-              if (xf_zero(rx) || rx.e + kXfTop < (long long)sh + 50) {
-                bool amb;
-                if (Kq >= Fs) {
-                  amb = true;
-                } else if ((long long)Kq <= len) {
-                  amb = cnt > 0;
-                } else {
-                  int c2 = 0;
-#pragma unroll
-                  for (int q = 0; q < kSegV; ++q) c2 += pref[q] < Kq - (unsigned long long)len ? 1 : 0;
-#pragma unroll
-                  for (int o = 16; o; o >>= 1) c2 += __shfl_xor_sync(0xFFFFFFFFu, c2, o);
-                  amb = c2 != cnt;
-                }
-                if (amb) {
-                  cnt = vec ? head_count<true>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
-                                                xf_make(rem.hi, rem.lo, ge), lane)
-                            : head_count<false>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
-                                                 xf_make(rem.hi, rem.lo, ge), lane);
+            if (mine) {
+              const u128 key = j0 == i ? kl : sm.key[j];
+              rem = u128_lt(Ps, key) ? u128_sub(key, Ps) : u128{0ULL, 0ULL};
+              Kq = ceil_units(rem, sh, Fs);
+              cnt = vec ? block_count<T, true>(sp, wk, (long long)sc * kSeg, Mk, E, Kq)
+                        : block_count<T, false>(sp, wk, (long long)sc * kSeg, Mk, E, Kq);
+            }
+            if (head) {  // warp-uniform branch; the ambiguous keys one by one
+              bool amb = false;
+              if (mine) {
+                const xf rx = xf_make(rem.hi, rem.lo, 0);
+                if (xf_zero(rx) || rx.e + kXfTop < (long long)sh + 50) {
+                  if (Kq >= Fs) amb = true;
+                  else if ((long long)Kq <= len) amb = cnt > 0;
+                  else
+                    amb = (vec ? block_count<T, true>(sp, wk, (long long)sc * kSeg, Mk, E, Kq - (unsigned long long)len)
+                               : block_count<T, false>(sp, wk, (long long)sc * kSeg, Mk, E,
+                                                       Kq - (unsigned long long)len)) != cnt;
                 }
               }
+              unsigned gx = __ballot_sync(0xFFFFFFFFu, amb);
+#pragma unroll 1
+              while (gx) {
+                const int jl = __ffs(gx) - 1;
+                gx &= gx - 1;
+                const u128 rj = shfl_v(rem, jl);
+                const int cj = vec ? head_count<true>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                      xf_make(rj.hi, rj.lo, ge), lane)
+                                   : head_count<false>(reinterpret_cast<const double*>(wk), (long long)sc * kSeg, Mk,
+                                                       xf_make(rj.hi, rj.lo, ge), lane);
+                if (lane == jl) cnt = cj;
+              }
             }
-            if (lane == 0) {
+            if (mine) {
               const int jj = cnt < len ? cnt : len - 1;
               long long idx = (long long)sc * kSeg + jj;
               if (idx > Mk - 1) idx = Mk - 1;
               outk[j] = (int)idx;
             }
           }
+          __syncwarp();
         } else {
+          // many samples: the whole segment's exact prefixes, staged in
+          // shared memory, and a binary search over them per sample
+          Bits b[kSegV];
+          if (pf == sc) {
+#pragma unroll
+            for (int q = 0; q < kSegV; ++q) b[q] = bn[q];
+          } else if (vec) {
+            load_seg_blocked<T, true>(wk, (long long)sc * kSeg, Mk, lane, b);
+          } else {
+            load_seg_blocked<T, false>(wk, (long long)sc * kSeg, Mk, lane, b);
+          }
+          pf = -1;
+          if (F32 && sc + 1 < sb) {  // the next segment's weights travel while this one is resolved
+            if (vec) load_seg_blocked<T, true>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+            else load_seg_blocked<T, false>(wk, (long long)(sc + 1) * kSeg, Mk, lane, bn);
+            pf = sc + 1;
+          }
+          uint64_t pref[kSegV];
+          seg_prefixes<T>(b, E, lane, pref);
           // the binary-search leaf over prefixes staged in shared memory
           __syncwarp();
 #pragma unroll
@@ -713,15 +793,14 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w
 #endif
 }
 
+// CTAs of a batched launch: K without a queue, else every CTA the device
+// holds at once (at most K).
 template <typename T, int kThreads>
-static cudaError_t batched_t(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
-                             unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
-                             int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
-                             const LogTab* tab) {
+static cudaError_t batched_blocks(int K, bool queue, long long& blocks) {
   const size_t smem = sizeof(BatchSmem<kThreads / 32>);
   cudaError_t e = cudaFuncSetAttribute(k_batched<T, kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  long long blocks = K;
+  blocks = K;
   if (queue) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched<T, kThreads>, kThreads, smem);
@@ -731,8 +810,20 @@ static cudaError_t batched_t(const T* w, const long long* w_off, const long long
     if (blocks > K) blocks = K;
   }
   if (blocks < 1) blocks = 1;
+  return cudaSuccess;
+}
+
+template <typename T, int kThreads>
+static cudaError_t batched_t(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
+                             unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
+                             int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
+                             const LogTab* tab, unsigned long long* lpref) {
+  long long blocks = 0;
+  cudaError_t e = batched_blocks<T, kThreads>(K, queue != nullptr, blocks);
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(BatchSmem<kThreads / 32>);
   k_batched<T, kThreads><<<(unsigned)blocks, kThreads, smem, st>>>(w, w_off, r_off, order, K, seed, inst_base, M0, N0,
-                                                                    leaf_T, out, queue, status, scheme, tab);
+                                                                    leaf_T, out, queue, status, scheme, tab, lpref);
   return cudaGetLastError();
 }
 
@@ -740,30 +831,44 @@ template <typename T>
 static cudaError_t batched_dispatch(const T* w, const long long* w_off, const long long* r_off, const int* order, int K,
                                     unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
                                     int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st,
-                                    int scheme, const LogTab* tab) {
+                                    int scheme, const LogTab* tab, unsigned long long* lpref) {
   switch (threads) {
     case 128:
       return batched_t<T, 128>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
-                               scheme, tab);
+                               scheme, tab, lpref);
     case 512:
       return batched_t<T, 512>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
-                               scheme, tab);
+                               scheme, tab, lpref);
     default:
       return batched_t<T, 256>(w, w_off, r_off, order, K, seed, inst_base, M0, N0, leaf_T, out, queue, status, st,
-                               scheme, tab);
+                               scheme, tab, lpref);
   }
+}
+
+size_t batched_scratch_bytes(bool f32, int threads, int K, bool queue) {
+  long long blocks = 0;
+  cudaError_t e;
+  if (f32) {
+    e = threads == 128 ? batched_blocks<float, 128>(K, queue, blocks)
+        : threads == 512 ? batched_blocks<float, 512>(K, queue, blocks) : batched_blocks<float, 256>(K, queue, blocks);
+  } else {
+    e = threads == 128 ? batched_blocks<double, 128>(K, queue, blocks)
+        : threads == 512 ? batched_blocks<double, 512>(K, queue, blocks) : batched_blocks<double, 256>(K, queue, blocks);
+  }
+  if (e != cudaSuccess) return 0;
+  return (size_t)blocks * kBMaxSeg * 32 * sizeof(unsigned long long);
 }
 
 cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, const long long* r_off, const int* order,
                            int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
                            int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
-                           const LogTab* tab) {
+                           const LogTab* tab, unsigned long long* lpref) {
   if (K <= 0) return cudaSuccess;
   if (f32)
     return batched_dispatch<float>(static_cast<const float*>(w), w_off, r_off, order, K, seed, inst_base, M0, N0,
-                                   threads, leaf_T, out, queue, status, st, scheme, tab);
+                                   threads, leaf_T, out, queue, status, st, scheme, tab, lpref);
   return batched_dispatch<double>(static_cast<const double*>(w), w_off, r_off, order, K, seed, inst_base, M0, N0,
-                                  threads, leaf_T, out, queue, status, st, scheme, tab);
+                                  threads, leaf_T, out, queue, status, st, scheme, tab, lpref);
 }
 
 size_t small_smem_bytes(bool f32) { return f32 ? sizeof(SmallSmem<float>) : sizeof(SmallSmem<double>); }

@@ -113,9 +113,13 @@ __device__ __forceinline__ uint64_t fixed64_valid(uint64_t b, uint32_t E) {
   return ((uint64_t)xhi << 32) | rlo;
 }
 
-template <typename T>
-__device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits (&b)[kSegV], int lane, int* status,
-                                             uint64_t& F, uint32_t& E) {
+// The exact segment sum F and exponent E described above; also the sums of
+// this lane's elements in consecutive groups of kG (g[j]: elements kG j ..
+// kG j + kG - 1 of b; the groups of all lanes add up to F).
+template <typename T, int kG>
+__device__ __forceinline__ void seg_sum_bits_groups(const typename FixedTraits<T>::Bits (&b)[kSegV], int lane,
+                                                    int* status, uint64_t& F, uint32_t& E,
+                                                    uint64_t (&g)[kSegV / kG]) {
   using Tr = FixedTraits<T>;
   // the largest sign+exponent field: below the all-ones exponent only when
   // every element is a non-negative finite number
@@ -124,15 +128,16 @@ __device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits
   for (int i = 0; i < kSegV; ++i) tmax = max(tmax, Tr::top(b[i]));
   tmax = __reduce_max_sync(0xFFFFFFFFu, tmax);
   constexpr uint32_t kTopInf = sizeof(T) == 8 ? 0x7FFu : 0xFFu;
-  uint64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kSegV / kG; ++j) g[j] = 0;
   if (tmax < kTopInf) {
     E = tmax > 1u ? tmax : 1u;
     if (sizeof(T) == 8) {
 #pragma unroll
-      for (int i = 0; i < kSegV; ++i) sum += fixed64_valid((uint64_t)b[i], E);
+      for (int i = 0; i < kSegV; ++i) g[i / kG] += fixed64_valid((uint64_t)b[i], E);
     } else {
 #pragma unroll
-      for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+      for (int i = 0; i < kSegV; ++i) g[i / kG] += Tr::fixed(b[i], E);
     }
   } else {
     // rare: negative zeros (valid), or negative, NaN or infinite weights,
@@ -148,9 +153,18 @@ __device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits
     E = emax > 1u ? emax : 1u;
     if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) raise_status(status, ST_ENONFINITE);
 #pragma unroll
-    for (int i = 0; i < kSegV; ++i) sum += Tr::fixed(b[i], E);
+    for (int i = 0; i < kSegV; ++i) g[i / kG] += Tr::fixed(b[i], E);
   }
+  uint64_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kSegV / kG; ++j) sum += g[j];
   F = warp_sum_u64(sum);
+}
+template <typename T>
+__device__ __forceinline__ void seg_sum_bits(const typename FixedTraits<T>::Bits (&b)[kSegV], int lane, int* status,
+                                             uint64_t& F, uint32_t& E) {
+  uint64_t g[1];
+  seg_sum_bits_groups<T, kSegV>(b, lane, status, F, E, g);
 }
 template <typename T, bool kVec>
 __device__ __forceinline__ void seg_sum(const T* __restrict__ w, long long base, long long M, int lane, int* status,

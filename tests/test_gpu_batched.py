@@ -79,7 +79,7 @@ def _per_instance(g, h, w, woff, roff, seed, prec=None):
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("threads", [128, 256, 512])
-@pytest.mark.parametrize("leaf", [1, 4, 32])
+@pytest.mark.parametrize("leaf", [1, 4, 32, 1024])
 def test_batched_equals_per_instance_bit_exact(g, h, threads, leaf, prec):
     w, woff, roff = _mixed_batch(11)
     p = g.RS_F32_COMP if prec == "f32" else g.RS_F64
@@ -172,7 +172,7 @@ def test_autotune_batched(g, h):
     w, woff, roff = workloads.weights_batched(K=64, seed=6, nmin=32, nmax=512, pmax=32)
     out = torch.empty(int(roff[-1]), dtype=torch.int32, device="cuda")
     best = g.rs_autotune_batched(h.h, dev(w), dev(woff), dev(roff), 64, 3, out, woff, roff)
-    assert best.tile_threads in (128, 256, 512) and best.leaf_L in (1, 4, 32)
+    assert best.tile_threads in (128, 256, 512) and best.leaf_L in (4, 16, 64)
     ref = _per_instance(g, h, w, woff, roff, seed=3)
     out2 = torch.full((int(roff[-1]),), -1, dtype=torch.int32, device="cuda")
     g.rs_resample_batched(h.h, dev(w), dev(woff), dev(roff), 64, 3, out2, woff, roff)  # uses the tuned values
