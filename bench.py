@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-measurements (e2e, map only, batched, bootstrap, stress)")
+    ap.add_argument("--batched-probe", type=int, default=0, metavar="K",
+                    help="only run the batched launch on the first K instances of the batched workload "
+                         "(binary32, default settings; 3 + 2 launches) and print their times: a small "
+                         "case for profiling the persistent kernel")
     ap.add_argument("--path", choices=["fused", "multikernel"], default="fused",
                     help="rs_resample_w as one cooperative launch (default) or through the "
                          "multi-kernel path (identical indices; for profiling and comparison)")
@@ -830,8 +834,40 @@ def cpu_allcore():
     return res
 
 
+def batched_probe(K):
+    """The persistent batched launch on the first K instances of the batched
+    workload (binary32 weights, default settings): three warm-up launches,
+    then two, each timed with CUDA events; prints one line."""
+    import torch
+    import paper_2604_01356_gb300 as g
+    wl = workloads.make("batched")
+    K = min(K, wl.info["K"])
+    woff, roff = wl.woff[:K + 1].copy(), wl.roff[:K + 1].copy()
+    wd = torch.from_numpy(wl.w[: int(woff[-1])]).cuda()
+    wo, ro = torch.from_numpy(woff).cuda(), torch.from_numpy(roff).cuda()
+    out = torch.empty(int(roff[-1]), dtype=torch.int32, device="cuda")
+    h = g.Handle()
+    ev = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.rs_resample_batched(h.h, wd, wo, ro, K, wl.seed, out, woff, roff, g.opts(prec=g.RS_F32_COMP))
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the batched probe")
+    h.close()
+    print(json.dumps({"batched_probe": {"K": K, "sum_M": int(woff[-1]), "sum_N": int(roff[-1]),
+                                        "algorithmic_bytes": 4 * int(woff[-1]) + 4 * int(roff[-1]),
+                                        "us": [round(a.elapsed_time(b) * 1e3, 1) for a, b in ev]}}))
+
+
 def main():
     args = parse()
+    if args.batched_probe:
+        batched_probe(args.batched_probe)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
