@@ -132,8 +132,9 @@ rs_status rs_destroy(rs_handle* h);
  *  W_out   [M] binary64 cumulative weights W (Eq. 3), written if not NULL.
  *  seed, instance select the Philox stream of the N+1 draws.
  * Launch forms, all giving identical indices: an instance of at most 12,288
- * weights and 2,047 samples runs on one CTA with its weights staged in
- * shared memory; one of at most 32,768
+ * weights and 2,047 samples runs with its weights staged in shared memory on
+ * one CTA, or from 384 samples on a cluster of four CTAs (each making a
+ * quarter of the draws and mapping those samples); one of at most 32,768
  * weights and 2,048 samples on one CTA reading them from global memory
  * (one launch each); otherwise one cooperative launch of one CTA per SM (a
  * multi-kernel sequence when the device cannot hold that grid, or when W_out

@@ -79,6 +79,9 @@ constexpr long long kSmallM = 1LL << 15;
 // Default leaf threshold of the persistent kernel (segments with at most
 // this many samples are decided from lane prefixes and one weight block).
 constexpr int kBatchedLeafDefault = 16;
+// From this many samples the shared-memory one-CTA form runs as a cluster of
+// four CTAs (the draws, keys and map split four ways).
+constexpr long long kSmallClusterN = 384;
 
 rs_status fail(rs_handle* h, rs_status s, const std::string& msg) {
   if (h) h->err = msg;
@@ -767,7 +770,7 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
     // shared memory
     RS_TRACE(h, "small_smem", st);
     RS_CK(h, launch_small(f32, w, M, N, seed, instance, out_idx, h->status, st, o.scheme,
-                          static_cast<const LogTab*>(h->logtab)));
+                          static_cast<const LogTab*>(h->logtab), N >= kSmallClusterN ? 4 : 1));
     return RS_OK;
   }
   if (N > 0 && !W_out && !(o.debug & 6) && M <= kSmallM && N <= kBMaxN) {

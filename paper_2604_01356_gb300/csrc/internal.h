@@ -173,8 +173,11 @@ constexpr int kSmThreads = 512;
 constexpr long long kSmallMaxN = 2047;
 constexpr long long kSmallMaxM = 12288;
 size_t small_smem_bytes(bool f32);
+// cluster: 1 (one CTA) or 4 (a cluster of four CTAs on four SMs, each
+// making a quarter of the draws and mapping those samples).
 cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,
-                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab);
+                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab,
+                         int cluster);
 // The sampling steps (Algorithm 1 + the map named by algo: 0 divide and
 // conquer, 1 binary search, 2 linear walk) on one CTA with W in shared memory: M <= kSmallMaxM, N <= kSmallMaxN; the
 // indices equal those of the multi-launch form.

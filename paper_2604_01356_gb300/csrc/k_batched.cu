@@ -539,10 +539,33 @@ struct SmallSmem {
   unsigned long long F[kMaxSeg];
   int E[kMaxSeg];
   u128 wsum[kSmThreads / 32];
+  u128 part;  // this CTA's spacing total, read by the other CTAs of a cluster
   xf c, invZ;
   int emax_w[kSmThreads / 32];
   LogTab tab;
 };
+
+// Thread-block cluster helpers (a cluster of kG CTAs, one per SM).
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster; orders the shared-memory
+// writes before it against the other CTAs' reads after it.
+__device__ __forceinline__ void cluster_sync_all() {
+  __syncwarp();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The u128 at the same shared-memory offset as p in CTA `rank` of the cluster.
+__device__ __forceinline__ u128 ld_cluster_u128(const u128* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  unsigned long long lo, hi;
+  asm volatile("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(ra) : "memory");
+  return u128{lo, hi};
+}
 
 // Shared-memory position of entry e of an array of 8-byte (kPer = 2) or
 // 4-byte (kPer = 4) entries: 16-byte chunks are swizzled within each
@@ -562,7 +585,13 @@ __device__ __forceinline__ int count_below_sw(const unsigned long long* P, long 
   return pos + (P[sm_word<2>(base + pos)] < X ? 1 : 0);
 }
 
-template <typename T>
+// kG > 1: a cluster of kG CTAs shares the instance.  CTA r makes the draws
+// [k_a, k_b) (Philox blocks split evenly) and maps those samples; the kG
+// spacing totals are exchanged once through distributed shared memory (the
+// offset of this CTA's prefixes and Z_{N+1}); every CTA stages all the
+// weights and decodes every segment itself, so nothing else crosses CTAs and
+// the arithmetic is that of kG = 1.
+template <typename T, int kG>
 __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w, long long M, long long N,
                                                          unsigned long long seed, unsigned long long inst,
                                                          int* __restrict__ out, int* status, int scheme,
@@ -595,23 +624,30 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w
   __syncthreads();
   GBR_BSTAMP(true, 0);
 
-  // ---- Algorithm 1: all N + 1 spacings in one tile, exact prefixes Z_i ------
-  // Multinomial draws with N + 1 <= 1024 take two per thread (one Philox
-  // block serves two threads), else four (one block per thread).
+  // ---- Algorithm 1: this CTA's spacings in one tile, exact prefixes --------
+  // Multinomial draws: two per thread when the CTA holds at most 1024 (one
+  // Philox block serves two threads), else four (one block per thread).
   const long long ndraw = N + 1;
+  const int rank = kG > 1 ? (int)cluster_rank() : 0;
+  const long long nblk = (ndraw + 3) / 4;
+  const long long ka = 4 * (nblk * rank / kG);
+  const long long kb = rank == kG - 1 ? ndraw : 4 * (nblk * (rank + 1) / kG);
+  const long long ns = (kb < N ? kb : N) - ka;  // this CTA's samples [ka, ka + ns)
+  u128 zoff = {0ULL, 0ULL};                     // spacings of the CTAs before this one
   {
-    const int dpt = (scheme == kSchemeMultinomial && ndraw <= 2 * kSmThreads) ? 2 : 4;
-    const long long k0 = (long long)dpt * tid;
+    const int dpt = (scheme == kSchemeMultinomial && kb - ka <= 2 * kSmThreads) ? 2 : 4;
+    const long long k0 = ka + (long long)dpt * tid;
     uint64_t wd[4] = {0ULL, 0ULL, 0ULL, 0ULL};
-    if (k0 < ndraw) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
+    if (k0 < kb) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
     u128 f[4];
     if (dpt == 2) {
       const int o = (int)(k0 & 3);  // 0 or 2
-      f[0] = k0 < ndraw ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
-      f[1] = k0 + 1 < ndraw ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
+      f[0] = k0 < kb ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
+      f[1] = k0 + 1 < kb ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
       f[2] = f[3] = u128{0ULL, 0ULL};
     } else {
       block_spacings<F32>(scheme, k0, ndraw, seed, inst, wd, &sm.tab, f);
+      if (k0 >= kb) f[0] = f[1] = f[2] = f[3] = u128{0ULL, 0ULL};  // another CTA's draws
     }
     u128 run = {0ULL, 0ULL}, inc[4];
 #pragma unroll
@@ -633,7 +669,19 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w
     off = u128_add(off, u128_sub(incl, run));
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      if (q < dpt && k0 + q < N) sm.key[k0 + q] = u128_add(off, inc[q]);
+      if (q < dpt && k0 + q < ka + ns) sm.key[k0 + q - ka] = u128_add(off, inc[q]);
+    if (kG > 1) {
+      // the CTAs' spacing totals: this CTA's offset and Z_{N+1}
+      if (tid == 0) sm.part = tot;
+      cluster_sync_all();
+      tot = u128{0ULL, 0ULL};
+#pragma unroll
+      for (int r = 0; r < kG; ++r) {
+        const u128 v = ld_cluster_u128(&sm.part, (unsigned)r);
+        if (r < rank) zoff = u128_add(zoff, v);
+        tot = u128_add(tot, v);
+      }
+    }
     // 1 / Z_{N+1} on warp 15 from here on, while warps 0-14 take the segments
     if (tid == kSegThreads) sm.invZ = recip_total(tot);
   }
@@ -716,17 +764,18 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w
   __syncthreads();
   GBR_BSTAMP(true, 4);
   if (u128_is_zero(sm.pre[nseg])) {
-    if (tid == 0) raise_status(status, ST_EZEROSUM);
-    for (long long i = tid; i < N; i += kSmThreads) out[i] = 0;
+    if (tid == 0 && rank == 0) raise_status(status, ST_EZEROSUM);
+    for (long long i = tid; i < ns; i += kSmThreads) out[ka + i] = 0;
+    if (kG > 1) cluster_sync_all();  // no CTA leaves while another may read its shared memory
     return;
   }
   const xf c = sm.c;
-  for (long long i = tid; i < N; i += kSmThreads) sm.key[i] = map_key(c, sm.key[i]);
+  for (long long i = tid; i < ns; i += kSmThreads) sm.key[i] = map_key(c, u128_add(zoff, sm.key[i]));
   __syncthreads();
   GBR_BSTAMP(true, 5);
 
-  // ---- the map (Eq. 2 by Algorithm 5's split argument, one CTA) --------------
-  const long long i0 = N * warp / kWarps, i1 = N * (warp + 1) / kWarps;
+  // ---- the map (Eq. 2 by Algorithm 5's split argument) of this CTA's samples -
+  const long long i0 = ns * warp / kWarps, i1 = ns * (warp + 1) / kWarps;
 #pragma unroll 1
   for (long long r0 = i0; r0 < i1; r0 += 32) {
     const long long i = r0 + lane;
@@ -784,13 +833,14 @@ __global__ void __launch_bounds__(kSmThreads, 1) k_small(const T* __restrict__ w
       const int jj = cnt < len ? cnt : len - 1;
       long long idx = (long long)s_me * kSeg + jj;
       if (idx > M - 1) idx = M - 1;
-      out[i] = (int)idx;
+      out[ka + i] = (int)idx;
     }
   }
 #ifdef GBR_PHASE_STAMPS
   __syncthreads();
   GBR_BSTAMP(true, 6);
 #endif
+  if (kG > 1) cluster_sync_all();  // no CTA leaves while another may read its shared memory
 }
 
 // CTAs of a batched launch: K without a queue, else every CTA the device
@@ -873,24 +923,44 @@ cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, cons
 
 size_t small_smem_bytes(bool f32) { return f32 ? sizeof(SmallSmem<float>) : sizeof(SmallSmem<double>); }
 
+template <typename T, int kG>
+static cudaError_t small_t(const T* w, long long M, long long N, unsigned long long seed, unsigned long long inst,
+                           int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab) {
+  const size_t smem = sizeof(SmallSmem<T>);
+  cudaError_t e = cudaFuncSetAttribute(k_small<T, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (kG == 1) {
+    k_small<T, 1><<<1, kSmThreads, smem, st>>>(w, M, N, seed, inst, out, status, scheme, tab);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kG, 1, 1);
+  cfg.blockDim = dim3(kSmThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kG;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_small<T, kG>, w, M, N, seed, inst, out, status, scheme, tab);
+}
+
 cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,
-                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab) {
+                         unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab,
+                         int cluster) {
   if (N <= 0 || M <= 0) return cudaSuccess;
   if (N > kSmallMaxN || M > kSmallMaxM) return cudaErrorInvalidValue;
-  const size_t smem = small_smem_bytes(f32);
-  cudaError_t e;
   if (f32) {
-    e = cudaFuncSetAttribute(k_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_small<float><<<1, kSmThreads, smem, st>>>(static_cast<const float*>(w), M, N, seed, inst, out, status, scheme,
-                                                 tab);
-  } else {
-    e = cudaFuncSetAttribute(k_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_small<double><<<1, kSmThreads, smem, st>>>(static_cast<const double*>(w), M, N, seed, inst, out, status,
-                                                  scheme, tab);
+    if (cluster == 4)
+      return small_t<float, 4>(static_cast<const float*>(w), M, N, seed, inst, out, status, st, scheme, tab);
+    return small_t<float, 1>(static_cast<const float*>(w), M, N, seed, inst, out, status, st, scheme, tab);
   }
-  return cudaGetLastError();
+  if (cluster == 4)
+    return small_t<double, 4>(static_cast<const double*>(w), M, N, seed, inst, out, status, st, scheme, tab);
+  return small_t<double, 1>(static_cast<const double*>(w), M, N, seed, inst, out, status, st, scheme, tab);
 }
 
 // ---- work order: instances by M_k descending (ties by index) ----------------
