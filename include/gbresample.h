@@ -151,8 +151,8 @@ rs_status rs_resample_w(rs_handle* h, const void* w, int64_t M, int64_t N, uint6
  *          (not checked: a U above W_M is clamped to M-1).
  *  out_idx [N] int32, written.  opts->algo selects the map.
  * Launch forms, all giving identical indices: M <= 12,288 and N <= 2,047 run
- * on one CTA (W staged in shared memory, the DaC leaves one per thread unless
- * opts->leaf_L is set); otherwise the sorted uniforms (one CTA up to 2,047
+ * with W staged in shared memory on one CTA, or from 384 samples on a cluster
+ * of four CTAs (the DaC leaves one per thread unless opts->leaf_L is set); otherwise the sorted uniforms (one CTA up to 2,047
  * samples, else a look-back scan) and then the map kernel. */
 rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uint64_t seed, uint64_t instance,
                         int32_t* out_idx, const rs_opts* opts, void* stream);

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libgbresample.so")
 BUILD = os.path.join(ROOT, "_build")
 SOURCES = ["api.cu", "k_uniform.cu", "k_weights.cu", "k_map.cu", "k_batched.cu", "k_fused.cu", "k_gather.cu", "k_logw.cu", "static_uniform.cu"]
-HEADERS = ["common.cuh", "internal.h", "seg_common.cuh", "map_common.cuh"]
+HEADERS = ["common.cuh", "internal.h", "seg_common.cuh", "map_common.cuh", "cluster.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -ftz=false: binary32 arithmetic keeps subnormals (the binary32-pair
 # logarithm and exponential rely on exact two-sum and FMA error terms, which

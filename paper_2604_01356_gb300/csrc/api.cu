@@ -857,10 +857,11 @@ rs_status rs_resample_W(rs_handle* h, const double* W, int64_t M, int64_t N, uin
   if (M <= kSmallMaxM && N <= kSmallMaxN && !(o.debug & 5)) {
     // a small instance: the uniforms and the map on one CTA, W in shared
     // memory; the DaC leaves are one per thread unless opts->leaf_L is set
-    const int L = o.leaf_L > 0 ? o.leaf_L : (int)((N + kSmallThreadsW - 1) / kSmallThreadsW);
+    const int G = N >= kSmallClusterN ? 4 : 1;
+    const int L = o.leaf_L > 0 ? o.leaf_L : (int)((N + (long long)kSmallThreadsW * G - 1) / ((long long)kSmallThreadsW * G));
     RS_TRACE(h, "small_W", st);
     RS_CK(h, launch_small_W(o.prec == RS_F32_COMP, o.algo, W, M, N, seed, instance, L, out_idx, st, o.scheme,
-                            static_cast<const LogTab*>(h->logtab)));
+                            static_cast<const LogTab*>(h->logtab), G));
     return RS_OK;
   }
   const Plan p = make_plan(0, N, false, true, true);

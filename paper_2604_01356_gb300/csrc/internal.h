@@ -179,11 +179,13 @@ cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsi
                          unsigned long long inst, int* out, int* status, cudaStream_t st, int scheme, const LogTab* tab,
                          int cluster);
 // The sampling steps (Algorithm 1 + the map named by algo: 0 divide and
-// conquer, 1 binary search, 2 linear walk) on one CTA with W in shared memory: M <= kSmallMaxM, N <= kSmallMaxN; the
+// conquer, 1 binary search, 2 linear walk) on one CTA or (cluster 4) a
+// cluster of four with W in shared memory: M <= kSmallMaxM, N <= kSmallMaxN; the
 // indices equal those of the multi-launch form.
 constexpr int kSmallThreadsW = 512;
 cudaError_t launch_small_W(bool f32, int algo, const double* W, long long M, long long N, unsigned long long seed,
-                           unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab);
+                           unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab,
+                           int cluster);
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_linear(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st);
 cudaError_t launch_map_dac(const double* W, long long M, const double* U, long long N, int L, int stage_max, int* out,

@@ -27,6 +27,9 @@
 //
 // Instances with more than kBMaxSeg segments or kBMaxN samples are not
 // processed here (the host sends them through the single-instance path).
+#include <cstddef>
+
+#include "cluster.cuh"
 #include "map_common.cuh"
 
 // Phase timestamps (profiling builds only, -DGBR_PHASE_STAMPS): %globaltimer
@@ -539,33 +542,15 @@ struct SmallSmem {
   unsigned long long F[kMaxSeg];
   int E[kMaxSeg];
   u128 wsum[kSmThreads / 32];
-  u128 part;  // this CTA's spacing total, read by the other CTAs of a cluster
+  alignas(16) u128 part;  // this CTA's spacing total, read by the other CTAs of a cluster (16-byte loads)
   xf c, invZ;
   int emax_w[kSmThreads / 32];
   LogTab tab;
 };
 
-// Thread-block cluster helpers (a cluster of kG CTAs, one per SM).
-__device__ __forceinline__ unsigned cluster_rank() {
-  unsigned r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// Every thread of every CTA of the cluster; orders the shared-memory
-// writes before it against the other CTAs' reads after it.
-__device__ __forceinline__ void cluster_sync_all() {
-  __syncwarp();
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// The u128 at the same shared-memory offset as p in CTA `rank` of the cluster.
-__device__ __forceinline__ u128 ld_cluster_u128(const u128* p, unsigned rank) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  unsigned ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-  unsigned long long lo, hi;
-  asm volatile("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "r"(ra) : "memory");
-  return u128{lo, hi};
-}
+
+static_assert(offsetof(SmallSmem<double>, part) % 16 == 0 && offsetof(SmallSmem<float>, part) % 16 == 0,
+              "16-byte cluster loads of part");
 
 // Shared-memory position of entry e of an array of 8-byte (kPer = 2) or
 // 4-byte (kPer = 4) entries: 16-byte chunks are swizzled within each

@@ -22,6 +22,9 @@
 // Comparisons on a given binary64 W are exact: values are compared through
 // their total-order integer keys, which agree with IEEE comparison for every
 // non-NaN value, so all three maps return bit-identical indices.
+#include <cstddef>
+
+#include "cluster.cuh"
 #include "map_common.cuh"
 
 namespace gbr {
@@ -265,9 +268,11 @@ struct SmallWSmem {
   long long Wk[kSmallMaxM];  // W's bits, then their total-order keys
   long long Uk[kSmallMaxN];  // the keys of U
   u128 wsum[kSwThreads / 32];
+  alignas(16) u128 part;  // this CTA's spacing total, read by the other CTAs of a cluster (16-byte loads)
   xf r;
   LogTab tab;
 };
+static_assert(offsetof(SmallWSmem, part) % 16 == 0, "16-byte cluster loads of part");
 __device__ __forceinline__ long long lower_bound_sm(const long long* Wk, long long a, long long b, long long key) {
   while (a < b) {  // smallest m in [a, b] with Wk[m] >= key, else b
     const long long m = (a + b) >> 1;
@@ -277,7 +282,11 @@ __device__ __forceinline__ long long lower_bound_sm(const long long* Wk, long lo
   return b;
 }
 
-template <bool F32, int kAlgo>
+// kG > 1: a cluster of kG CTAs; CTA r makes the draws of its share of the
+// Philox blocks, forms U for those samples and maps them against its own copy
+// of W; the spacing totals are exchanged once through distributed shared
+// memory, so U is exactly that of one CTA.
+template <bool F32, int kAlgo, int kG>
 __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restrict__ W, long long M, long long N,
                                                            unsigned long long seed, unsigned long long inst, int L,
                                                            int* __restrict__ out, int scheme,
@@ -302,20 +311,26 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restr
 
   // ---- Algorithm 1, exactly as the one-CTA uniform kernel ------------------
   const long long ndraw = N + 1;
-  const int dpt = (scheme == kSchemeMultinomial && ndraw <= 2 * kSwThreads) ? 2 : 4;
-  const long long k0 = (long long)dpt * tid;
+  const int rank = kG > 1 ? (int)cluster_rank() : 0;
+  const long long nblk = (ndraw + 3) / 4;
+  const long long ka = 4 * (nblk * rank / kG);
+  const long long kb = rank == kG - 1 ? ndraw : 4 * (nblk * (rank + 1) / kG);
+  const long long ns = (kb < N ? kb : N) - ka;  // this CTA's samples [ka, ka + ns)
+  const int dpt = (scheme == kSchemeMultinomial && kb - ka <= 2 * kSwThreads) ? 2 : 4;
+  const long long k0 = ka + (long long)dpt * tid;
   u128 z[4];
   {
     uint64_t wd[4] = {0ULL, 0ULL, 0ULL, 0ULL};
-    if (k0 < ndraw) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
+    if (k0 < kb) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
     u128 f[4];
     if (dpt == 2) {
       const int o = (int)(k0 & 3);
-      f[0] = k0 < ndraw ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
-      f[1] = k0 + 1 < ndraw ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
+      f[0] = k0 < kb ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
+      f[1] = k0 + 1 < kb ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
       f[2] = f[3] = u128{0ULL, 0ULL};
     } else {
       block_spacings<F32>(scheme, k0, ndraw, seed, inst, wd, &sm.tab, f);
+      if (k0 >= kb) f[0] = f[1] = f[2] = f[3] = u128{0ULL, 0ULL};  // another CTA's draws
     }
     u128 run = {0ULL, 0ULL};
 #pragma unroll
@@ -334,6 +349,18 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restr
       tot = u128_add(tot, t);
     }
     off = u128_add(off, u128_sub(incl, run));
+    if (kG > 1) {
+      // the CTAs' spacing totals: this CTA's offset and Z_{N+1}
+      if (tid == 0) sm.part = tot;
+      cluster_sync_all();
+      tot = u128{0ULL, 0ULL};
+#pragma unroll
+      for (int r = 0; r < kG; ++r) {
+        const u128 v = ld_cluster_u128(&sm.part, (unsigned)r);
+        if (r < rank) off = u128_add(off, v);
+        tot = u128_add(tot, v);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) z[q] = u128_add(off, z[q]);  // Z_{k0+q+1}
     if (tid == kCopyThreads) sm.r = u128_is_zero(tot) ? lb_zero<xf>() : recip_total(tot);
@@ -350,27 +377,28 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restr
     const xf r = sm.r;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (q < dpt && k0 + q < N) {
+      if (q < dpt && k0 + q < ka + ns) {
         long long ub = (long long)xf_to_f64_bits(xf_mul_u128(r, z[q]));
         if (ub > 0x3FF0000000000000LL) ub = 0x3FF0000000000000LL;
-        sm.Uk[k0 + q] = ord_key_bits(ub);
+        sm.Uk[k0 + q - ka] = ord_key_bits(ub);
       }
     }
   }
   __syncthreads();
 
-  // ---- the map ----------------------------------------------------------------
+  // ---- the map of this CTA's samples (local index i is sample ka + i) ----------
   const long long* Wk = sm.Wk;
   const long long* Uk = sm.Uk;
+  int* outk = out + ka;
   if (kAlgo == kMapBinary) {
-    for (long long i = tid; i < N; i += kSwThreads) out[i] = (int)lower_bound_sm(Wk, 0, M - 1, Uk[i]);
+    for (long long i = tid; i < ns; i += kSwThreads) outk[i] = (int)lower_bound_sm(Wk, 0, M - 1, Uk[i]);
   } else if (kAlgo == kMapLinear) {
     const long long a = M * tid / kSwThreads, b = M * (tid + 1) / kSwThreads;
     if (a < b) {
       // the slice's samples: W[a-1] < U_i <= W[b-1] (the last slice: all above W[a-1])
       long long i = 0;
       if (a > 0) {
-        long long lo = 0, hi = N;
+        long long lo = 0, hi = ns;
         while (lo < hi) {
           const long long m = (lo + hi) >> 1;
           if (Uk[m] <= Wk[a - 1]) lo = m + 1;
@@ -380,56 +408,74 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restr
       }
       const bool last = b == M;
       long long j = a;
-      for (; i < N; ++i) {
+      for (; i < ns; ++i) {
         const long long k = Uk[i];
         if (!last && k > Wk[b - 1]) break;
         while (j < M - 1 && Wk[j] < k) ++j;
-        out[i] = (int)j;
+        outk[i] = (int)j;
       }
     }
   } else {
-    const long long nleaf = (N + L - 1) / L;
+    const long long nleaf = (ns + L - 1) / L;
     for (long long leaf = tid; leaf < nleaf; leaf += kSwThreads) {
       const long long a = leaf * (long long)L;
-      const long long b = (a + L < N ? a + L : N) - 1;
+      const long long b = (a + L < ns ? a + L : ns) - 1;
       const long long rb = lower_bound_sm(Wk, 0, M - 1, Uk[b]);
       long long j = lower_bound_sm(Wk, 0, rb, Uk[a]);
-      out[a] = (int)j;
+      outk[a] = (int)j;
       for (long long i = a + 1; i <= b; ++i) {
         const long long k = Uk[i];
         while (j < rb && Wk[j] < k) ++j;
-        out[i] = (int)j;
+        outk[i] = (int)j;
       }
     }
   }
+  if (kG > 1) cluster_sync_all();  // no CTA leaves while another may read its shared memory
 }
 
-template <bool F32>
+template <bool F32, int kAlgo, int kG>
+static cudaError_t small_W_go(const double* W, long long M, long long N, unsigned long long seed,
+                              unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab) {
+  const size_t smem = sizeof(SmallWSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_small_W<F32, kAlgo, kG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (kG == 1) {
+    k_small_W<F32, kAlgo, 1><<<1, kSwThreads, smem, st>>>(W, M, N, seed, inst, L, out, scheme, tab);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kG, 1, 1);
+  cfg.blockDim = dim3(kSwThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kG;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_small_W<F32, kAlgo, kG>, W, M, N, seed, inst, L, out, scheme, tab);
+}
+
+template <bool F32, int kG>
 static cudaError_t small_W_t(int algo, const double* W, long long M, long long N, unsigned long long seed,
                              unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab) {
-  const size_t smem = sizeof(SmallWSmem);
-  cudaError_t e;
-#define GBR_SMALL_W(A)                                                                                         \
-  e = cudaFuncSetAttribute(k_small_W<F32, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
-  if (e != cudaSuccess) return e;                                                                              \
-  k_small_W<F32, A><<<1, kSwThreads, smem, st>>>(W, M, N, seed, inst, L, out, scheme, tab);
-  if (algo == kMapBinary) {
-    GBR_SMALL_W(kMapBinary)
-  } else if (algo == kMapLinear) {
-    GBR_SMALL_W(kMapLinear)
-  } else {
-    GBR_SMALL_W(kMapDac)
-  }
-#undef GBR_SMALL_W
-  return cudaGetLastError();
+  if (algo == kMapBinary) return small_W_go<F32, kMapBinary, kG>(W, M, N, seed, inst, L, out, st, scheme, tab);
+  if (algo == kMapLinear) return small_W_go<F32, kMapLinear, kG>(W, M, N, seed, inst, L, out, st, scheme, tab);
+  return small_W_go<F32, kMapDac, kG>(W, M, N, seed, inst, L, out, st, scheme, tab);
 }
 
 cudaError_t launch_small_W(bool f32, int algo, const double* W, long long M, long long N, unsigned long long seed,
-                           unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab) {
+                           unsigned long long inst, int L, int* out, cudaStream_t st, int scheme, const LogTab* tab,
+                           int cluster) {
   if (N <= 0 || M <= 0) return cudaSuccess;
   if (N > kSmallMaxN || M > kSmallMaxM || L < 1) return cudaErrorInvalidValue;
-  return f32 ? small_W_t<true>(algo, W, M, N, seed, inst, L, out, st, scheme, tab)
-             : small_W_t<false>(algo, W, M, N, seed, inst, L, out, st, scheme, tab);
+  if (cluster == 4)
+    return f32 ? small_W_t<true, 4>(algo, W, M, N, seed, inst, L, out, st, scheme, tab)
+               : small_W_t<false, 4>(algo, W, M, N, seed, inst, L, out, st, scheme, tab);
+  return f32 ? small_W_t<true, 1>(algo, W, M, N, seed, inst, L, out, st, scheme, tab)
+             : small_W_t<false, 1>(algo, W, M, N, seed, inst, L, out, st, scheme, tab);
 }
 
 cudaError_t launch_map_binary(const double* W, long long M, const double* U, long long N, int* out, cudaStream_t st) {
