@@ -930,7 +930,11 @@ static cudaError_t small_t(const T* w, long long M, long long N, unsigned long l
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_small<T, kG>, w, M, N, seed, inst, out, status, scheme, tab);
+  e = cudaLaunchKernelEx(&cfg, k_small<T, kG>, w, M, N, seed, inst, out, status, scheme, tab);
+  if (e == cudaSuccess) return e;
+  // a device that cannot place the cluster: the one-CTA form (same indices)
+  (void)cudaGetLastError();
+  return small_t<T, 1>(w, M, N, seed, inst, out, status, st, scheme, tab);
 }
 
 cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,

@@ -455,7 +455,11 @@ static cudaError_t small_W_go(const double* W, long long M, long long N, unsigne
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_small_W<F32, kAlgo, kG>, W, M, N, seed, inst, L, out, scheme, tab);
+  e = cudaLaunchKernelEx(&cfg, k_small_W<F32, kAlgo, kG>, W, M, N, seed, inst, L, out, scheme, tab);
+  if (e == cudaSuccess) return e;
+  // a device that cannot place the cluster: the one-CTA form (same indices)
+  (void)cudaGetLastError();
+  return small_W_go<F32, kAlgo, 1>(W, M, N, seed, inst, L, out, st, scheme, tab);
 }
 
 template <bool F32, int kG>
