@@ -166,13 +166,12 @@ cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, cons
                            int K, unsigned long long seed, unsigned long long inst_base, long long M0, long long N0,
                            int threads, int leaf_T, int* out, unsigned* queue, int* status, cudaStream_t st, int scheme,
                            const LogTab* tab, unsigned long long* lpref);
-// --- one-CTA whole path of a small instance, weights staged in shared memory
-// (512 threads; N + 1 <= 2048 draws in one tile; at most kSmallMaxM
-// weights).  Indices equal those of every other form of rs_resample_w.
+// --- the whole path of a small instance, weights staged in shared memory
+// (512 threads a CTA; N + 1 <= 2048 draws; at most kSmallMaxM weights).
+// Indices equal those of every other form of rs_resample_w.
 constexpr int kSmThreads = 512;
 constexpr long long kSmallMaxN = 2047;
 constexpr long long kSmallMaxM = 12288;
-size_t small_smem_bytes(bool f32);
 // cluster: 1 (one CTA) or 4 (a cluster of four CTAs on four SMs, each
 // making a quarter of the draws and mapping those samples).
 cudaError_t launch_small(bool f32, const void* w, long long M, long long N, unsigned long long seed,

@@ -906,7 +906,6 @@ cudaError_t launch_batched(bool f32, const void* w, const long long* w_off, cons
                                   threads, leaf_T, out, queue, status, st, scheme, tab, lpref);
 }
 
-size_t small_smem_bytes(bool f32) { return f32 ? sizeof(SmallSmem<float>) : sizeof(SmallSmem<double>); }
 
 template <typename T, int kG>
 static cudaError_t small_t(const T* w, long long M, long long N, unsigned long long seed, unsigned long long inst,
