@@ -67,6 +67,10 @@ def parse():
                     help="only run the batched launch on the first K instances of the batched workload "
                          "(binary32, default settings; 3 + 2 launches) and print their times: a small "
                          "case for profiling the persistent kernel")
+    ap.add_argument("--small-probe", action="store_true",
+                    help="only run rs_resample_w and rs_resample_W (binary search) on the small workload "
+                         "(M = 4096, N = 1024), 3 + 2 calls each, and print their times: a small case for "
+                         "profiling the shared-memory kernels")
     ap.add_argument("--path", choices=["fused", "multikernel"], default="fused",
                     help="rs_resample_w as one cooperative launch (default) or through the "
                          "multi-kernel path (identical indices; for profiling and comparison)")
@@ -863,8 +867,43 @@ def batched_probe(K):
                                         "us": [round(a.elapsed_time(b) * 1e3, 1) for a, b in ev]}}))
 
 
+def small_probe():
+    """rs_resample_w, then rs_resample_W with the binary-search map, on the
+    small workload: three warm-up calls each, then two timed with CUDA
+    events; prints one line."""
+    import torch
+    import oracle
+    import paper_2604_01356_gb300 as g
+    oracle.lib()
+    wl = workloads.make("small")
+    wd = torch.from_numpy(wl.w).cuda()
+    W = torch.from_numpy(oracle.cumulative(wl.w)[0]).cuda()
+    out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
+    h = g.Handle()
+    res = {}
+    for name, fn in [("resample_w", lambda: g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out)),
+                     ("resample_W_binary", lambda: g.rs_resample_W(h.h, W, wl.M, wl.N, wl.seed, 0, out,
+                                                                   g.opts(algo=g.RS_MAP_BINARY)))]:
+        ev = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        res[name] = [round(a.elapsed_time(b) * 1e3, 1) for a, b in ev]
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the small probe")
+    h.close()
+    print(json.dumps({"small_probe": {"M": wl.M, "N": wl.N, "us": res}}))
+
+
 def main():
     args = parse()
+    if args.small_probe:
+        small_probe()
+        return
     if args.batched_probe:
         batched_probe(args.batched_probe)
         return
