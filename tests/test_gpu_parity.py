@@ -481,6 +481,40 @@ def test_small_smem_adversarial(g, h, kind, M, N):
     assert np.array_equal(host(a), host(b))
 
 
+@pytest.mark.parametrize("N", [300, 1024])
+def test_small_smem_error_paths(g, N):
+    """The shared-memory small-instance forms (one CTA below 384 samples, a
+    cluster of four from there) latch RS_EZEROSUM with zero indices for an
+    all-zero instance, and RS_ENONFINITE for a NaN weight; the handle keeps
+    working afterwards."""
+    M = 4096
+    out = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+    hz = g.Handle()
+    try:
+        g.rs_resample_w(hz.h, dev(np.zeros(M)), M, N, 3, 0, out)
+        assert hz.status() == g.RS_EZEROSUM
+        assert np.all(host(out) == 0)
+    finally:
+        hz.close()
+    w = workloads.weights_lognormal(M, 2.0, seed=5)
+    w[1234] = np.nan
+    hn = g.Handle()
+    try:
+        g.rs_resample_w(hn.h, dev(w), M, N, 3, 0, out)
+        assert hn.status() == g.RS_ENONFINITE
+    finally:
+        hn.close()
+    hk = g.Handle()
+    try:
+        w[1234] = 1.0
+        g.rs_resample_w(hk.h, dev(w), M, N, 3, 0, out)
+        assert hk.status() == g.RS_OK
+        r = host(out)
+        assert r.min() >= 0 and r.max() < M and np.all(np.diff(r) >= 0)
+    finally:
+        hk.close()
+
+
 def test_small_smem_is_taken(g, h):
     """The small workload's shape (M = 4096, N = 1024) runs on the
     shared-memory one-CTA form; 20,000 binary64 weights on the other one."""
