@@ -37,21 +37,33 @@ def softmax_gpu(g, h, l):
     return w
 
 
-@pytest.mark.parametrize("sigma,M", [(1.0, 1), (2.0, 513), (2.0, 100_003), (10.0, 1_000_000), (100.0, 50_000)])
-def test_softmax_weights_accuracy(g, h, sigma, M):
-    l = np.random.default_rng(M).normal(0.0, sigma, size=M) + 3.0
+@pytest.mark.parametrize("sigma,M,shift", [(1.0, 1, 3.0), (2.0, 513, 3.0), (2.0, 100_003, 3.0),
+                                           (10.0, 1_000_000, 3.0), (100.0, 50_000, 3.0),
+                                           (1e-3, 20_000, 0.0), (50.0, 30_000, -1e6), (2.0, 30_000, 4e4)])
+def test_softmax_weights_accuracy(g, h, sigma, M, shift):
+    l = np.random.default_rng(M).normal(0.0, sigma, size=M) + shift
     w = host(softmax_gpu(g, h, l))
     assert h.status() == g.RS_OK
     ref = oracle.softmax_weights(l)
     x = l - l.max()
-    # the GPU takes exp of the exact l - m in binary32 pairs (about 2^-44
+    # the GPU takes exp of the exact l - m in integer arithmetic (below 2^-49
     # relative); the oracle rounds l - m to binary64 first, which moves exp by
     # up to 2^-53 |l - m| relative, and its exp by about 2^-52; subnormal
     # results to an absolute 2^-1060
-    tol = np.maximum((2.0 ** -44 + 2.0 ** -52 * (np.abs(x) + 1.0)) * ref, 2.0 ** -1060)
+    tol = np.maximum((2.0 ** -48 + 2.0 ** -52 * (np.abs(x) + 1.0)) * ref, 2.0 ** -1060)
     bad = np.abs(w - ref) > tol
     assert not bad.any(), (x[bad][:3], w[bad][:3], ref[bad][:3])
     assert w[np.argmax(l)] == 1.0
+
+
+def test_softmax_subnormal_band(g, h):
+    """Results from 2^-1022 down to the underflow to 0 (x in [-746, -700])."""
+    l = np.concatenate([[0.0], -700.0 - 46.0 * np.random.default_rng(3).random(20_000)])
+    w = host(softmax_gpu(g, h, l))
+    assert h.status() == g.RS_OK
+    ref = oracle.softmax_weights(l)
+    assert np.all(np.abs(w - ref) <= np.maximum(2.0 ** -1072, 2.0 ** -46 * ref))
+    assert np.all(w[l < -745.2] == 0.0)
 
 
 def test_softmax_special_values(g, h):
