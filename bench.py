@@ -60,7 +60,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip everything that runs the oracle: the CPU baselines (one core, all cores), "
+                         "the paper sweep's serial CPU maps and the accuracy report against the oracle")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the sub-measurements (e2e, map only, batched, bootstrap, stress)")
     ap.add_argument("--batched-probe", type=int, default=0, metavar="K",
@@ -71,6 +73,10 @@ def parse():
                     help="only run rs_resample_w and rs_resample_W (binary search) on the small workload "
                          "(M = 4096, N = 1024), 3 + 2 calls each, and print their times: a small case for "
                          "profiling the shared-memory kernels")
+    ap.add_argument("--logw-probe", action="store_true",
+                    help="only run rs_resample_logw on the engmf log-weights (M = 16,777,216 binary64, "
+                         "N = 4,096), 3 + 2 calls, and print their times: a case for profiling the "
+                         "maximum and exponent passes")
     ap.add_argument("--path", choices=["fused", "multikernel"], default="fused",
                     help="rs_resample_w as one cooperative launch (default) or through the "
                          "multi-kernel path (identical indices; for profiling and comparison)")
@@ -341,7 +347,8 @@ def run_ours(args):
             line["map_only"] = map_only(g, h, wl, dev, stream)
             line["gather"] = gather_measure(g, h, dev, stream, hbm)
             line["logw"] = logw_measure(g, h, dev, stream, hbm)
-            line["paper_sweep"] = paper_sweep(g, h, dev, stream)
+            if not args.no_cpu_baseline:  # its CPU half is the oracle's serial maps
+                line["paper_sweep"] = paper_sweep(g, h, dev, stream)
             del wd, flush, graph
             torch.cuda.empty_cache()
             line["batched"] = batched_measure(g, h, dev, stream, hbm)
@@ -349,7 +356,8 @@ def run_ours(args):
             line["bootstrap"] = single_measure(g, h, dev, stream, "bootstrap", hbm)
             line["stress"] = single_measure(g, h, dev, stream, "stress", hbm)
             line["small"] = small_measure(g, h, dev, stream)
-            line["accuracy_vs_oracle"] = accuracy_report(g, h, dev, stream)
+            if not args.no_cpu_baseline:  # the oracle as the checker
+                line["accuracy_vs_oracle"] = accuracy_report(g, h, dev, stream)
     else:
         line["e2e"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -484,8 +492,9 @@ def paper_sweep(g, h, dev, stream, reps=20):
         for N in (100, 316, 1000, 3162, 10000):
             M = N * ratio
             w = workloads.weights_lognormal(M, 2.0, seed=1000 + N + ratio)
-            W, _ = oracle.cumulative(w)
-            Wd = torch.from_numpy(W).to(dev)
+            Wd = torch.empty(M, dtype=torch.float64, device=dev)
+            g.rs_cumulative(h.h, torch.from_numpy(w).to(dev), M, Wd, stream=stream)  # the GPU leg's W
+            W, _ = oracle.cumulative(w)  # the serial CPU algorithms' W
             out = torch.empty(N, dtype=torch.int32, device=dev)
             row = {"N": N, "M": M}
             for name, algo in [("dac", g.RS_MAP_DAC), ("binary", g.RS_MAP_BINARY), ("linear", g.RS_MAP_LINEAR)]:
@@ -667,12 +676,11 @@ def small_measure(g, h, dev, stream, reps=200):
     sampling steps on a given W (sorted uniforms + each of the three maps,
     rs_resample_W), as per-call microseconds; a launch-latency regime."""
     import torch
-    import oracle
-    oracle.lib()
     wl = workloads.make("small")
     M, N, seed = wl.M, wl.N, wl.seed
     wd = torch.from_numpy(wl.w).to(dev)
-    W = torch.from_numpy(oracle.cumulative(wl.w)[0]).to(dev)
+    W = torch.empty(M, dtype=torch.float64, device=dev)
+    g.rs_cumulative(h.h, wd, M, W, stream=stream)  # W for the sampling steps, by the library
     out = torch.empty(N, dtype=torch.int32, device=dev)
     res = {"M": M, "N": N, "bytes": 8 * M + 4 * N,
            "timing": "*_us_per_call: back-to-back calls from Python (includes the host's issue cost per call); "
@@ -872,14 +880,13 @@ def small_probe():
     small workload: three warm-up calls each, then two timed with CUDA
     events; prints one line."""
     import torch
-    import oracle
     import paper_2604_01356_gb300 as g
-    oracle.lib()
     wl = workloads.make("small")
     wd = torch.from_numpy(wl.w).cuda()
-    W = torch.from_numpy(oracle.cumulative(wl.w)[0]).cuda()
     out = torch.empty(wl.N, dtype=torch.int32, device="cuda")
     h = g.Handle()
+    W = torch.empty(wl.M, dtype=torch.float64, device="cuda")
+    g.rs_cumulative(h.h, wd, wl.M, W)  # W for the sampling steps, by the library
     res = {}
     for name, fn in [("resample_w", lambda: g.rs_resample_w(h.h, wd, wl.M, wl.N, wl.seed, 0, out)),
                      ("resample_W_binary", lambda: g.rs_resample_W(h.h, W, wl.M, wl.N, wl.seed, 0, out,
@@ -899,8 +906,35 @@ def small_probe():
     print(json.dumps({"small_probe": {"M": wl.M, "N": wl.N, "us": res}}))
 
 
+def logw_probe():
+    """rs_resample_logw on the engmf log-weights: three warm-up calls, then
+    two timed with CUDA events; prints one line."""
+    import torch
+    import paper_2604_01356_gb300 as g
+    c = workloads.CONFIGS["engmf"]
+    M, N = c["M"], c["N"]
+    l = torch.from_numpy(np.random.default_rng(c["seed"]).normal(0.0, 2.0, size=M)).cuda()
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    h = g.Handle()
+    ev = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.rs_resample_logw(h.h, l, M, N, 12, 0, out)
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    if h.status() != g.RS_OK:
+        raise RuntimeError("device status after the log-weight probe")
+    h.close()
+    print(json.dumps({"logw_probe": {"M": M, "N": N, "us": [round(a.elapsed_time(b) * 1e3, 1) for a, b in ev]}}))
+
+
 def main():
     args = parse()
+    if args.logw_probe:
+        logw_probe()
+        return
     if args.small_probe:
         small_probe()
         return
