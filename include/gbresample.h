@@ -227,9 +227,11 @@ rs_status rs_philox(rs_handle* h, uint64_t seed, uint64_t instance, uint64_t fir
  * w_out[j] = exp(logw[j] - max_k logw[k]), binary64, the largest weight 1.
  *  logw  [M] binary64 log-weights, device; -inf gives a zero weight.
  *  w_out [M] binary64, written (may not overlap logw).
- * Computed without binary64 arithmetic per element: the exponent is
- * evaluated in binary32 pairs (relative error about 2^-44 of the binary64
- * value; subnormal results are truncated).  NaN, +inf or |l| >= 2^126
+ * Computed without binary64 arithmetic per element: the exponential is
+ * evaluated in 64-bit integer arithmetic from the difference l - m in fixed
+ * point (relative error below 2^-49.5 of the binary64 value, about 2^-52 when
+ * |l|, |m| >= 1; subnormal results within 2 units of 2^-1074, and 0 below
+ * exp(-745.14)).  NaN, +inf or |l| >= 2^126
  * latch RS_ENONFINITE; all -inf latches RS_EZEROSUM (rs_get_status).
  * Two passes over logw (maximum, then exponent) and one write of w_out. */
 rs_status rs_softmax_weights(rs_handle* h, const double* logw, int64_t M, double* w_out, void* stream);
