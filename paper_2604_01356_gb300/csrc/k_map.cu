@@ -303,27 +303,41 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_small_W(const double* __restr
       cp_async16(sm.Wk + 2 * q, reinterpret_cast<const char*>(W) + 16 * q);
     cp_async_commit();
   }
-  for (int i = tid; i < 129; i += kSwThreads) {
-    sm.tab.nlogc[i] = tab->nlogc[i];
-    sm.tab.invc[i] = tab->invc[i];
+  // the logarithm table: loaded now, stored to shared memory after the
+  // Philox blocks (which do not need it)
+  float2 tnl = {0.0f, 0.0f}, tic = {0.0f, 0.0f};
+  if (tid < 129) {
+    tnl = tab->nlogc[tid];
+    tic = tab->invc[tid];
   }
-  __syncthreads();
 
   // ---- Algorithm 1, exactly as the one-CTA uniform kernel ------------------
+  // Multinomial draws: one per thread when the CTA holds at most 512, two when
+  // at most 1024, else four (one Philox block per thread).
   const long long ndraw = N + 1;
   const int rank = kG > 1 ? (int)cluster_rank() : 0;
   const long long nblk = (ndraw + 3) / 4;
   const long long ka = 4 * (nblk * rank / kG);
   const long long kb = rank == kG - 1 ? ndraw : 4 * (nblk * (rank + 1) / kG);
   const long long ns = (kb < N ? kb : N) - ka;  // this CTA's samples [ka, ka + ns)
-  const int dpt = (scheme == kSchemeMultinomial && kb - ka <= 2 * kSwThreads) ? 2 : 4;
+  const int dpt = scheme != kSchemeMultinomial ? 4 : kb - ka <= kSwThreads ? 1 : kb - ka <= 2 * kSwThreads ? 2 : 4;
   const long long k0 = ka + (long long)dpt * tid;
   u128 z[4];
   {
     uint64_t wd[4] = {0ULL, 0ULL, 0ULL, 0ULL};
     if (k0 < kb) philox4x64_10((uint64_t)(k0 / 4), 0ULL, 0ULL, 0ULL, seed, inst, wd);
+    if (tid < 129) {
+      sm.tab.nlogc[tid] = tnl;
+      sm.tab.invc[tid] = tic;
+    }
+    __syncthreads();
     u128 f[4];
-    if (dpt == 2) {
+    if (dpt == 1) {
+      const int o = (int)(k0 & 3);
+      const uint64_t x = o == 0 ? wd[0] : o == 1 ? wd[1] : o == 2 ? wd[2] : wd[3];
+      f[0] = k0 < kb ? spacing_fixed<F32>(x, &sm.tab) : u128{0ULL, 0ULL};
+      f[1] = f[2] = f[3] = u128{0ULL, 0ULL};
+    } else if (dpt == 2) {
       const int o = (int)(k0 & 3);
       f[0] = k0 < kb ? spacing_fixed<F32>(o ? wd[2] : wd[0], &sm.tab) : u128{0ULL, 0ULL};
       f[1] = k0 + 1 < kb ? spacing_fixed<F32>(o ? wd[3] : wd[1], &sm.tab) : u128{0ULL, 0ULL};
