@@ -231,31 +231,21 @@ __device__ __forceinline__ uint64_t philox_word(unsigned long long seed, unsigne
 // Product of two xf, out of line: one copy of the 128x128-bit multiply for
 // the scalar (once per call) paths.
 static __device__ __noinline__ xf xf_mul_ool(xf a, xf b) { return xf_mul(a, b); }
-// 1 / Z_{N+1} (Z_{N+1} > 0), by Newton's iteration y <- y (2 - u y) for the
-// mantissa u in [1, 2): a binary32 estimate (about 2^-22), two steps on the
-// top 64 bits of u in 64-bit fixed point (to about 2^-62), then one step on
-// the whole 128-bit mantissa, which squares the error (relative error below
-// 2^-122.5, the truncations of the products included).  No binary64
-// instruction: on this part they would make the single-thread chain several
-// times longer.
+// 1 / Z_{N+1} (Z_{N+1} > 0): a binary64 estimate of the reciprocal of the
+// top 64 mantissa bits (relative error below 2^-51), then two Newton steps
+// r <- r (2 - m r) on the 128-bit mantissa, each squaring the relative error
+// (2^-51 -> 2^-102 -> the 2^-124 truncation floor of the products).  Integer
+// work only, apart from the one estimate.
 static __device__ __noinline__ xf recip_total(u128 t) {
-  const xf m = xf_make(t.hi, t.lo, 0);                      // t = M 2^e, top bit of M at 125
-  const unsigned long long U = (m.hi << 2) | (m.lo >> 62);  // u = U 2^-63, truncated
-  const float uf = __uint2float_rn((unsigned)(U >> 40)) * 0x1p-23f;
-  float yf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(uf));
-  unsigned long long Y = __float2ull_rn(yf * 0x1p63f);  // 2^63 / u, Y <= 2^63
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    // D = 2^126 - Y U (small, signed); Y += Y D 2^-126
-    const unsigned long long plo = Y * U, phi = __umul64hi(Y, U);
-    const unsigned long long dlo = 0ULL - plo, dhi = (1ULL << 62) - phi - (plo != 0ULL ? 1ULL : 0ULL);
-    const long long Ds = (long long)((dhi << 2) | (dlo >> 62));  // D 2^-62
-    Y = (unsigned long long)((long long)Y + __mul64hi((long long)Y, Ds));
-  }
-  xf r = xf_make(0ULL, Y, -63 - kXfTop - m.e);  // 1/t = (Y 2^-63) 2^(-125 - e)
+  const xf m = xf_make(t.hi, t.lo, 0);  // t = (hi:lo) 2^e, top mantissa bit at 125
+  const unsigned long long top = (m.hi << 2) | (m.lo >> 62);
+  const double y = 1.0 / __ull2double_rn(top);  // ~ 2^-(62 + e) / m
+  xf r = xf_from_f64_bits((uint64_t)__double_as_longlong(y));
+  r.e -= 62 + m.e;
   const xf two = xf_from_u64(2, 0);
-  return xf_mul(r, xf_sub(two, xf_mul(m, r)));
+#pragma unroll 1
+  for (int k = 0; k < 2; ++k) r = xf_mul_ool(r, xf_sub(two, xf_mul_ool(m, r)));
+  return r;
 }
 
 // ---- one tile of the spacing scan ------------------------------------------
