@@ -492,8 +492,9 @@ def paper_sweep(g, h, dev, stream, reps=20):
         for N in (100, 316, 1000, 3162, 10000):
             M = N * ratio
             w = workloads.weights_lognormal(M, 2.0, seed=1000 + N + ratio)
+            wdev = torch.from_numpy(w).to(dev)  # kept alive while the side stream reads it
             Wd = torch.empty(M, dtype=torch.float64, device=dev)
-            g.rs_cumulative(h.h, torch.from_numpy(w).to(dev), M, Wd, stream=stream)  # the GPU leg's W
+            g.rs_cumulative(h.h, wdev, M, Wd, stream=stream)  # the GPU leg's W
             W, _ = oracle.cumulative(w)  # the serial CPU algorithms' W
             out = torch.empty(N, dtype=torch.int32, device=dev)
             row = {"N": N, "M": M}
