@@ -40,3 +40,38 @@ def test_reference_arm_other_ranks_silent():
     p = run_bench({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert p.stdout.strip() == ""
+
+
+def test_gpu_arm_runs_no_oracle():
+    """The GPU arm's measurements take their inputs from the workload
+    generators or the library itself: no function of that arm names the
+    oracle, and run_ours calls the oracle legs (CPU baselines, the paper
+    sweep's serial maps, the accuracy report) only under the CPU-baseline
+    switch."""
+    import ast
+    import inspect
+    sys.path.insert(0, ROOT)
+    import bench
+    for fn in (bench.e2e_measure, bench.map_only, bench.gather_measure, bench.logw_measure, bench.batched_measure,
+               bench.single_measure, bench.small_measure, bench.batched_probe, bench.small_probe, bench.logw_probe,
+               bench._time_calls, bench._time_graph_calls, bench.make_flush):
+        assert "oracle" not in inspect.getsource(fn), fn.__name__
+    tree = ast.parse(inspect.getsource(bench.run_ours))
+    legs = {"paper_sweep", "accuracy_report", "cpu_baseline", "cpu_allcore"}
+    gated = set()
+
+    def walk(node, under_switch):
+        if isinstance(node, ast.If) and "no_cpu_baseline" in ast.unparse(node.test):
+            for child in node.body:
+                walk(child, True)
+            for child in node.orelse:
+                walk(child, under_switch)
+            return
+        if isinstance(node, ast.Call) and isinstance(node.func, ast.Name) and node.func.id in legs:
+            assert under_switch, node.func.id
+            gated.add(node.func.id)
+        for child in ast.iter_child_nodes(node):
+            walk(child, under_switch)
+
+    walk(tree, False)
+    assert gated == legs
